@@ -1,0 +1,80 @@
+"""Plant plausible mistakes in a copy of the oracle source (on the CPU) and check
+that the pins of test_oracle_pins catch every one of them.
+
+Each mutation is a textual edit of lbm_oracle.c compiled into a temporary
+library; the oracle module is pointed at it for the duration of one check.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import build as OB
+from tests import _pins as P
+from tests import test_oracle_pins as T
+
+
+def _relaxation_identity():
+    T.test_cascaded_post_collision_central_moments_hit_relaxation_targets(T.OMEGA_SETS[1], True)
+
+
+def _source_moments():
+    T.test_source_central_moments_match_eq10()
+
+
+def _streaming():
+    for edges in T.EDGE_CASES:
+        T.test_streaming_with_walls_brute_force(edges, (5, 3))
+
+
+def _couette():
+    T.test_couette_moving_wall(O.CASCADED, 1e-12)
+
+
+def _conservation():
+    for m in (O.CASCADED, O.BGK, O.RAWMRT):
+        T.test_collision_conserves_mass_and_adds_force(m)
+
+
+def _unit_rates():
+    T.test_unit_rates_give_the_cascaded_equilibrium()
+
+
+def _mrt():
+    T.test_raw_mrt_relaxes_orthogonal_moments()
+
+
+MUTATIONS = [
+    # (name, original text, planted text, pin expected to fail)
+    ("sigma_xxy central reading (dropped source term in g6)",
+     "uy * kxx - 0.5 * sxxy)", "uy * kxx)", _relaxation_identity),
+    ("wrong sign of g5 in f~5", "(2.0 * g3 + g5 - g6 - g7 + g8)", "(2.0 * g3 - g5 - g6 - g7 + g8)",
+     _relaxation_identity),
+    ("kxyy in place of kxxy in g6", "+ kxxy - 2.0 * ux * kxy", "+ kxyy - 2.0 * ux * kxy",
+     _relaxation_identity),
+    ("dropped F/2 in the velocity", "*ux = (jx + 0.5 * F[0]) / r;", "*ux = jx / r;", _relaxation_identity),
+    ("wrong sign of m4 in S4", "(-6.0 * m2 - m3 - 9.0 * m4", "(-6.0 * m2 - m3 + 9.0 * m4", _source_moments),
+    ("wrong rest target of xxyy", "(1.0 / 9.0) * rho + 3.0", "(1.0 / 3.0) * rho + 3.0", _unit_rates),
+    ("lid correction with the wrong sign", "corr = 6.0 * W[b]", "corr = -6.0 * W[b]", _couette),
+    ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
+    ("transposed K in the raw-MRT projection", "m += KMAT[a][b] * fb[a];", "m += KMAT[b][a] * fb[a];",
+     _mrt),
+    ("omega_3 used for the deviatoric kernel", "(w4 / 4.0) * (rho * (ux * ux - uy * uy)",
+     "(w3 / 4.0) * (rho * (ux * ux - uy * uy)", _relaxation_identity),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, planted, pin):
+    src = open(OB.SRC).read()
+    assert src.count(orig) == 1, f"mutation anchor not unique for {name}"
+    mutant_c = tmp_path / "lbm_oracle.c"
+    mutant_c.write_text(src.replace(orig, planted))
+    lib = str(tmp_path / f"liblbm_oracle_mut{os.getpid()}.so")
+    subprocess.run(["gcc", *OB.CFLAGS, "-I", OB.HERE, str(mutant_c), "-o", lib, "-lm"], check=True)
+    pin()  # the unmutated oracle passes the pin
+    with O.substituted_library(lib):
+        with pytest.raises(AssertionError):
+            pin()

@@ -1,0 +1,336 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each check uses the printed
+tables (tests/golden/), direct moment summation, conservation laws, closed-form
+flows (Poiseuille, Couette, Taylor-Green) or brute force on tiny lattices.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import _pins as P
+
+OMEGA_SETS = [
+    (1.0, 1.25, 1.25, 1.0, 1.0, 1.0),
+    (1.3, 1.7, 1.6, 0.9, 1.1, 1.2),
+    (0.4, 1.95, 1.9, 1.5, 0.7, 1.8),
+]
+
+
+def _random_node(rng, u_amp=0.1, noise=0.05):
+    rho = 1.0 + 0.1 * rng.standard_normal()
+    u = u_amp * rng.standard_normal(2)
+    fb = O.equilibrium_node(O.CASCADED, rho, *u) * (1.0 + noise * rng.standard_normal(9))
+    return fb
+
+
+# ---------------------------------------------------------------- basis (Eq. 1-3, 15, 17)
+
+def test_k_matrix_is_built_from_the_monomials_of_eq2():
+    ex, ey = P.EX, P.EY
+    cols = [
+        np.ones(9), ex, ey, 3 * (ex ** 2 + ey ** 2) - 4, ex ** 2 - ey ** 2, ex * ey,
+        -3 * ex ** 2 * ey + 2 * ey, -3 * ex * ey ** 2 + 2 * ex,
+        9 * ex ** 2 * ey ** 2 - 6 * (ex ** 2 + ey ** 2) + 4,
+    ]
+    np.testing.assert_array_equal(np.stack(cols, axis=1), P.K)
+
+
+def test_columns_of_k_are_orthogonal():
+    # Reading: the text after Eq. (2) says K K^T is diagonal; it is K^T K that is.
+    KtK = P.K.T @ P.K
+    np.testing.assert_array_equal(KtK, np.diag([9, 6, 6, 36, 4, 4, 12, 12, 36]))
+    KKt = P.K @ P.K.T
+    assert np.abs(KKt - np.diag(np.diag(KKt))).max() > 0
+
+
+def test_collision_kernel_moments_eq17():
+    for row in P.KERNEL_MOMENTS:
+        m, n = int(row[0]), int(row[1])
+        coeff = [(P.K[:, b] * P.EX ** m * P.EY ** n).sum() for b in range(9)]
+        np.testing.assert_array_equal(coeff[3:], row[2:])
+
+
+def test_source_inversion_matrix_eq15_is_d_inverse_k_transpose():
+    # Reading: K^-1 = D^-1 K^T (Eq. 15 printed as K^T D^-1); 36 S_a = sum_b 36 K_ab m_b / D_b
+    D = np.diag(P.K.T @ P.K)
+    M = 36.0 * P.K / D[None, :]
+    np.testing.assert_allclose(M[:, 1:], P.SOURCE_MATRIX[:, 1:], atol=0)
+
+
+def test_weights_reading():
+    np.testing.assert_allclose(P.weights(), [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- per-node oracle pins
+
+def test_macros_node_definition():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        fb = _random_node(rng)
+        F = 1e-2 * rng.standard_normal(2)
+        rho, ux, uy = O.macros_node(fb, F)
+        assert rho == pytest.approx(fb.sum(), abs=1e-15)
+        assert ux == pytest.approx(((P.EX * fb).sum() + F[0] / 2) / fb.sum(), abs=1e-15)
+        assert uy == pytest.approx(((P.EY * fb).sum() + F[1] / 2) / fb.sum(), abs=1e-15)
+
+
+def test_source_central_moments_match_eq10():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        u = 0.2 * rng.standard_normal(2)
+        F = 0.05 * rng.standard_normal(2)
+        S = O.source_node(u, F)
+        cm = P.central_moments(S, *u)
+        np.testing.assert_allclose(cm, [0, F[0], F[1], 0, 0, 0, 0, 0, 0], atol=2e-16)
+        # Eq. (15) as printed (golden) reproduces S from its orthogonal moments
+        np.testing.assert_allclose(P.SOURCE_MATRIX @ (P.K.T @ S), 36 * S, atol=1e-15)
+
+
+def test_cascaded_equilibrium_central_moments():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        rho = 1 + 0.1 * rng.standard_normal()
+        u = 0.2 * rng.standard_normal(2)
+        feq = O.equilibrium_node(O.CASCADED, rho, *u)
+        np.testing.assert_allclose(P.central_moments(feq, *u),
+                                   rho * np.array([1, 0, 0, 1 / 3, 1 / 3, 0, 0, 0, 1 / 9]), atol=1e-15)
+    np.testing.assert_allclose(O.equilibrium_node(O.CASCADED, 1.0, 0, 0), P.weights(), atol=1e-16)
+
+
+def test_polynomial_equilibrium_moments():
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        rho = 1 + 0.1 * rng.standard_normal()
+        ux, uy = 0.1 * rng.standard_normal(2)
+        feq = O.equilibrium_node(O.BGK, rho, ux, uy)
+        r = P.raw_moments(feq)
+        np.testing.assert_allclose(r[:6], [rho, rho * ux, rho * uy, rho / 3 + rho * ux * ux,
+                                           rho / 3 + rho * uy * uy, rho * ux * uy], atol=1e-15)
+
+
+@pytest.mark.parametrize("om", OMEGA_SETS)
+@pytest.mark.parametrize("forced", [False, True])
+def test_cascaded_post_collision_central_moments_hit_relaxation_targets(om, forced):
+    """The cascaded collision relaxes each central moment (about the pre-collision
+    u) to its target at its own rate (Sec. II, Eq. 18-26)."""
+    rng = np.random.default_rng(7 + int(forced))
+    for _ in range(200):
+        fb = _random_node(rng)
+        F = (0.02 * rng.standard_normal(2)) if forced else np.zeros(2)
+        rho, ux, uy = O.macros_node(fb, F)
+        post = O.collide_node(O.CASCADED, fb, F, om)
+        pre_c = P.central_moments(fb, ux, uy)
+        np.testing.assert_allclose(P.central_moments(post, ux, uy),
+                                   P.relaxed_central(pre_c, rho, F, om), atol=2e-15)
+
+
+def test_cascaded_equals_central_moment_matrix_form():
+    """Independent formulation: build T(u), relax T f_bar, invert, add S."""
+    rng = np.random.default_rng(8)
+    for _ in range(100):
+        om = rng.uniform(0.2, 1.9, 6)
+        fb = _random_node(rng)
+        F = 0.02 * rng.standard_normal(2)
+        rho, ux, uy = O.macros_node(fb, F)
+        T = P.central_matrix(ux, uy)
+        c = P.relaxed_central(T @ fb, rho, (0.0, 0.0), om)
+        expect = np.linalg.solve(T, c) + O.source_node([ux, uy], F)
+        np.testing.assert_allclose(O.collide_node(O.CASCADED, fb, F, om), expect, atol=1e-14)
+
+
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_collision_conserves_mass_and_adds_force(model):
+    rng = np.random.default_rng(9)
+    for _ in range(100):
+        om = rng.uniform(0.2, 1.9, 6)
+        fb = _random_node(rng)
+        F = 0.02 * rng.standard_normal(2)
+        post = O.collide_node(model, fb, F, om)
+        assert post.sum() == pytest.approx(fb.sum(), abs=2e-15)
+        assert (P.EX * post).sum() - (P.EX * fb).sum() == pytest.approx(F[0], abs=2e-15)
+        assert (P.EY * post).sum() - (P.EY * fb).sum() == pytest.approx(F[1], abs=2e-15)
+
+
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_rest_state_is_a_fixed_point(model):
+    w = P.weights()
+    for om in OMEGA_SETS:
+        np.testing.assert_allclose(O.collide_node(model, 1.3 * w, (0, 0), om), 1.3 * w, atol=1e-16)
+
+
+def test_unit_rates_give_the_cascaded_equilibrium():
+    rng = np.random.default_rng(10)
+    for _ in range(50):
+        fb = _random_node(rng)
+        rho, ux, uy = O.macros_node(fb)
+        np.testing.assert_allclose(O.collide_node(O.CASCADED, fb, (0, 0), (1,) * 6),
+                                   O.equilibrium_node(O.CASCADED, rho, ux, uy), atol=1e-15)
+
+
+def test_bgk_unit_rate_gives_polynomial_equilibrium():
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        fb = _random_node(rng)
+        rho, ux, uy = O.macros_node(fb)
+        np.testing.assert_allclose(O.collide_node(O.BGK, fb, (0, 0), (1,) * 6),
+                                   O.equilibrium_node(O.BGK, rho, ux, uy), atol=1e-15)
+
+
+def test_raw_mrt_with_equal_rates_is_bgk():
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        w = rng.uniform(0.3, 1.9)
+        fb = _random_node(rng)
+        np.testing.assert_allclose(O.collide_node(O.RAWMRT, fb, (0, 0), (w,) * 6),
+                                   O.collide_node(O.BGK, fb, (0, 0), (w,) * 6), atol=2e-15)
+
+
+def test_raw_mrt_relaxes_orthogonal_moments():
+    rng = np.random.default_rng(13)
+    for _ in range(50):
+        om = rng.uniform(0.2, 1.9, 6)
+        fb = _random_node(rng)
+        F = 0.02 * rng.standard_normal(2)
+        rho, ux, uy = O.macros_node(fb, F)
+        feq = O.equilibrium_node(O.BGK, rho, ux, uy)
+        S = O.source_node([ux, uy], F)
+        lam = np.concatenate([[0, 0, 0], om])
+        m, meq, ms = P.K.T @ fb, P.K.T @ feq, P.K.T @ S
+        expect = m - lam * (m - meq) + (1 - lam / 2) * ms
+        np.testing.assert_allclose(P.K.T @ O.collide_node(O.RAWMRT, fb, F, om), expect, atol=1e-14)
+
+
+# ---------------------------------------------------------------- streaming and walls
+
+def test_periodic_streaming_is_a_shift():
+    rng = np.random.default_rng(14)
+    post = rng.standard_normal((9, 4, 5))
+    L = O.Lattice(5, 4, (1,) * 6)
+    L.stream(post)
+    for a in range(9):
+        np.testing.assert_array_equal(L.f[a], np.roll(post[a], (int(P.EY[a]), int(P.EX[a])), axis=(0, 1)))
+
+
+EDGE_CASES = [
+    (O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK),
+    (O.BOUNCEBACK, O.BOUNCEBACK, O.PERIODIC, O.PERIODIC),
+    (O.BOUNCEBACK, O.BOUNCEBACK, O.BOUNCEBACK, O.MOVING_WALL),
+    (O.MOVING_WALL, O.MOVING_WALL, O.MOVING_WALL, O.MOVING_WALL),
+    (O.PERIODIC, O.PERIODIC, O.MOVING_WALL, O.MOVING_WALL),
+]
+
+
+@pytest.mark.parametrize("edges", EDGE_CASES)
+@pytest.mark.parametrize("shape", [(5, 3), (4, 4), (1, 3), (3, 1)])
+def test_streaming_with_walls_brute_force(edges, shape):
+    nx, ny = shape
+    rng = np.random.default_rng(15)
+    post = rng.standard_normal((9, ny, nx))
+    wall_u = (0.03, -0.02, 0.05, 0.1)
+    L = O.Lattice(nx, ny, (1,) * 6, edges=edges, wall_u=wall_u)
+    L.stream(post)
+    np.testing.assert_allclose(L.f, P.stream_pull_reference(post, edges, wall_u), atol=1e-16)
+
+
+def test_cavity_conserves_mass():
+    L = O.Lattice(12, 10, (1, 1.6, 1.6, 1, 1, 1),
+                  edges=(O.BOUNCEBACK, O.BOUNCEBACK, O.BOUNCEBACK, O.MOVING_WALL), wall_u=(0, 0, 0, 0.1))
+    L.init()
+    m0 = L.f.sum()
+    L.run(300)
+    assert abs(L.f.sum() - m0) / m0 < 1e-14
+    _, u = L.macros()
+    assert np.abs(u).max() > 1e-3  # the lid has set the fluid in motion
+
+
+# ---------------------------------------------------------------- closed-form flows
+
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_poiseuille_channel(model):
+    """4x32 channel, periodic in x, half-way bounce-back walls, omega_shear = 1/0.8,
+    other rates 1, Fx = 8 nu Umax / H^2 with Umax = 0.01, 20000 steps from rest."""
+    om = 1 / 0.8
+    nu = O.nu_from_omega(om)
+    H = 32
+    fx = 8 * nu * 0.01 / H ** 2
+    L = O.Lattice(4, H, (1, om, om, 1, 1, 1), force=(fx, 0),
+                  edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK), model=model)
+    L.init().run(20000)
+    _, u = L.macros()
+    prof = u[0][:, 0]
+    ua = O.poiseuille_profile(H, fx, nu)
+    assert np.abs(prof - ua).max() / ua.max() < P.PAPER["poiseuille_max_rel_error"]["value"]
+    d2 = prof[2:] - 2 * prof[1:-1] + prof[:-2]
+    np.testing.assert_allclose(d2, -fx / nu, rtol=2e-6)       # exact parabola at steady state
+    assert np.abs(u[1]).max() < 1e-13
+    assert np.abs(u[0] - u[0][:, :1]).max() < 1e-15
+
+
+@pytest.mark.parametrize("model,tol", [(O.CASCADED, 1e-12), (O.BGK, 1e-10), (O.RAWMRT, 5e-4)])
+def test_couette_moving_wall(model, tol):
+    """Plane Couette flow: fixed south wall, north wall moving at U; the steady
+    profile is linear, u(y) = U (y + 1/2) / H between the half-way walls."""
+    U, om, H = 0.05, 1.2, 16
+    L = O.Lattice(3, H, (1, om, om, 1, 1, 1),
+                  edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.MOVING_WALL), wall_u=(0, 0, 0, U),
+                  model=model)
+    L.init().run(20000)
+    _, u = L.macros()
+    ua = U * (np.arange(H) + 0.5) / H
+    assert np.abs(u[0][:, 0] - ua).max() / U < tol
+    s = L.strain()
+    np.testing.assert_allclose(s[2], U / H, rtol=2e-2 if model == O.RAWMRT else 1e-6)
+
+
+def _tg_run(n, om=1.6, periods=1.0):
+    nu = O.nu_from_omega(om)
+    u0 = 0.04 * 64 / n
+    steps = int(round(periods * O.taylor_green_decay_time(n, nu)))
+    rho0, u_init, _ = O.taylor_green(n, u0, nu, 0)
+    L = O.Lattice(n, n, (1, om, om, 1, 1, 1)).init(rho0, u_init)
+    L.run(steps)
+    rho, u = L.macros()
+    _, ua, sa = O.taylor_green(n, u0, nu, steps)
+    sxx = L.strain()[0] / rho
+    return O.relative_l2(u, ua), O.relative_l2(sxx, sa), O.relative_error_paper(u, ua)
+
+
+def test_taylor_green_second_order_convergence():
+    """Diffusive scaling U0 = 0.04*64/N, omega = 1.6, one decay time: errors in u
+    and in S_xx from non-equilibrium moments fall as N^-2 (Sec. III-B)."""
+    res = [_tg_run(n) for n in (16, 32, 64)]
+    eu = np.array([r[0] for r in res])
+    es = np.array([r[1] for r in res])
+    su = np.log2(eu[:-1] / eu[1:])
+    ss = np.log2(es[:-1] / es[1:])
+    assert np.all((su > 1.9) & (su < 2.15)), su
+    assert np.all((ss > 1.9) & (ss < 2.15)), ss
+    assert res[-1][0] < 2e-3
+
+
+def test_complex_step_build_matches_real_build_and_fd():
+    """The complex build (used for complex-step gradients) agrees with the real
+    build on real inputs, and its derivative matches central differences."""
+    n, steps = 8, 25
+    rng = np.random.default_rng(16)
+    rho, u = 1 + 0.01 * rng.standard_normal((n, n)), 0.03 * rng.standard_normal((2, n, n))
+    om = (1.0, 1.6, 1.6, 1.0, 1.0, 1.0)
+
+    def loss(omega_shear, cplx):
+        oms = (1.0, omega_shear, omega_shear, 1.0, 1.0, 1.0)
+        L = O.Lattice(n, n, oms, complex=cplx, force=(1e-4, -2e-4)).init(rho, u)
+        L.run(steps)
+        _, uu = L.macros()
+        return 0.5 * (uu ** 2).sum()
+
+    r = O.Lattice(n, n, om).init(rho, u).run(steps)
+    c = O.Lattice(n, n, om, complex=True).init(rho, u).run(steps)
+    np.testing.assert_allclose(c.f.real, r.f, atol=1e-15)
+    h = 1e-30
+    d_cs = loss(1.6 + 1j * h, True).imag / h
+    e = 1e-6
+    d_fd = (loss(1.6 + e, False) - loss(1.6 - e, False)) / (2 * e)
+    assert d_cs == pytest.approx(d_fd, rel=1e-6)
