@@ -1,0 +1,403 @@
+"""Throughput of the fused cascaded D2Q9 update on one GB300 (and N replicas).
+
+Workload: decaying Taylor-Green vortex, 4096 x 4096 periodic nodes, diffusive
+scaling U0 = 0.04*64/4096, shear omega = 1.6, other rates 1 (the largest
+single-GPU Taylor-Green case).  One step = one lattice update of every node =
+one launch of the fused stream-and-collide kernel.  The populations (4096^2 x
+9 x 4 B = 604 MB in FP32) are far larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 cascaded MLUPS & % HBM roofline, FP16-store vs FP32 at stated error"
+N_DEFAULT = 4096
+OMEGA = 1.6
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_cascaded_tg4096.md")
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    p.add_argument("--no-extras", action="store_true", help="skip the sibling / precision comparison runs")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def omegas():
+    return (1.0, OMEGA, OMEGA, 1.0, 1.0, 1.0)
+
+
+def source_digest():
+    """Digest of the CUDA sources, used to tell whether a committed ncu summary
+    still describes the kernel being timed."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1202_6351_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(store_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current sources; else None."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"source digest:\s*`?([0-9a-f]+)", text)
+    if not m or m.group(1) != source_digest():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch\[{store_name}\]:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks sampler
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.samples = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.time()
+        while self.proc and not self.samples and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        inside = [p for (t, p) in self.samples if t0 <= t <= t1]
+        use = inside or [p for (_, p) in self.samples]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(p[1]) for p in use if num(p[1]) is not None]
+        smax = [num(p[2]) for p in use if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in use for k in range(4) if p[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside), "power_w_max": max(num(p[3]) or 0 for p in use)}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+
+def time_oracle(n_side, steps, max_seconds=None):
+    """Run the FP64 oracle on an n_side^2 Taylor-Green lattice; returns
+    (lattice updates per second, steps done, seconds)."""
+    import oracle as O
+    from paper_1202_6351_gb300 import workloads
+
+    rho, u = workloads.taylor_green_init(n_side, workloads.diffusive_u0(n_side))
+    L = O.Lattice(n_side, n_side, omegas()).init(rho, u)
+    done, t0 = 0, time.perf_counter()
+    chunk = max(1, min(steps, 10))
+    while done < steps:
+        k = min(chunk, steps - done)
+        L.run(k)
+        done += k
+        if max_seconds is not None and time.perf_counter() - t0 >= max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n_side * n_side * done / dt, done, dt
+
+
+def cpu_baseline_line(seconds=12.0):
+    side = 256
+    ups, done, dt = time_oracle(side, 10 ** 9, max_seconds=seconds)
+    return {"value": round(ups / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, Taylor-Green {side}x{side} cascaded, {done} steps in {dt:.1f} s "
+                      f"(one host thread)"}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each step: one oracle lattice update of a bounded Taylor-Green sample, sized
+    # so that warmup + steps take about a minute at ~10 MLUPS
+    budget_updates = 60.0 * 10e6
+    side = int(math.sqrt(budget_updates / max(1, args.steps + args.warmup)))
+    side = max(16, min(256, side // 16 * 16))
+    time_oracle(side, args.warmup)
+    ups, done, dt = time_oracle(side, args.steps)
+    v = ups / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / max(done, 1), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"taylor_green_{args.n}x{args.n}_cascaded", "sample": f"{side}x{side} per step",
+                   "omega_shear": OMEGA, "u0": 0.04 * 64 / args.n, "l2_flush": "none (CPU run)"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 C oracle, Taylor-Green {side}x{side}, {done} steps, one host thread"},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1202_6351_gb300 import lbm, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stores = {"f32": lbm.F32, "f16": lbm.F16DEV, "bf16": lbm.BF16DEV, "f64": lbm.F64}
+    store = stores[args.store]
+    n = args.n
+    nodes = n * n
+    u0 = workloads.diffusive_u0(n)
+    rho_h, u_h = workloads.taylor_green_init(n, u0)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def make(model=lbm.CASCADED, st=store):
+        L = lbm.Lattice(n, n, omegas(), model=model, store=st, stream=sp)
+        L.init(rho_h, u_h)
+        return L
+
+    def timed(L, steps, sampler=None):
+        """Warm-up already done; returns (seconds, t_wall0, t_wall1)."""
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        barrier()
+        return e0.elapsed_time(e1) / 1e3, w0, w1
+
+    peak, peak_kind = measured_peaks()
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+
+    # ---- the timed region: K steps of the cascaded kernel
+    L = make()
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if sampler:
+        sampler.wait_first()
+    L.step(args.warmup)
+    secs, w0, w1 = timed(L, args.steps)
+    if sampler:
+        time.sleep(0.3)
+        sampler.stop()
+    secs_t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(secs_t, op=dist.ReduceOp.MAX)
+    secs_max = float(secs_t.item())
+    value = world * nodes * args.steps / secs_max / 1e6
+    bpu = lbm.lbm_bytes_per_update(store)
+    launch_s = secs / args.steps
+    achieved = bpu * nodes / launch_s / 1e9
+    store_name = lbm.STORE_NAMES[store]
+    traffic = profiled_traffic(store_name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_update": bpu,
+                "algorithmic_bytes_per_launch": bpu * nodes}
+    L.close()
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(args, make, timed, lbm, nodes, peak, np)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if rank == 0:
+        e2e = run_e2e(args, lbm, torch, np, n, rho_h, u_h, sp, nodes)
+
+    if rank == 0:
+        clocks = sampler.summary(w0, w1) if sampler else None
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * secs_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if store != lbm.F64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"taylor_green_{n}x{n}_cascaded_{store_name}_store", "nodes": nodes,
+                       "omega_shear": OMEGA, "u0": u0, "model": "cascaded", "store": store_name,
+                       "l2_flush": f"none: populations {bpu // 2 * nodes / 1e6:.0f} MB > 129 MB L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "e2e": e2e,
+            "extras": extras,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_line()
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(args, make, timed, lbm, nodes, peak, np):
+    """Same workload with the other storage kinds and the sibling collisions
+    (separate timed regions, not part of `value`), plus the stated velocity
+    error of each storage kind against the FP64 run of the same steps."""
+    steps = max(200, min(args.steps, 2000))
+    out = {"steps": steps}
+    ref = make(lbm.CASCADED, lbm.F64)
+    ref.step(10)
+    s64, _, _ = timed(ref, steps)
+    _, u64 = ref.macros()
+    ref.close()
+    out["cascaded_f64"] = {"mlups": round(nodes * steps / s64 / 1e6, 1),
+                           "frac": round(lbm.lbm_bytes_per_update(lbm.F64) * nodes * steps / s64 / 1e9 / peak, 4)}
+    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV), ("bf16", lbm.BF16DEV)):
+        L = make(lbm.CASCADED, st)
+        L.step(10)
+        s, _, _ = timed(L, steps)
+        _, u = L.macros()
+        L.close()
+        err = float(np.sqrt(((u - u64) ** 2).sum() / (u64 ** 2).sum()))
+        out[f"cascaded_{name}"] = {
+            "mlups": round(nodes * steps / s / 1e6, 1),
+            "frac": round(lbm.lbm_bytes_per_update(st) * nodes * steps / s / 1e9 / peak, 4),
+            "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10}
+    for name, model in (("bgk", lbm.BGK), ("rawmrt", lbm.RAWMRT)):
+        L = make(model, lbm.F32)
+        L.step(10)
+        s, _, _ = timed(L, steps)
+        L.close()
+        out[f"{name}_f32"] = {"mlups": round(nodes * steps / s / 1e6, 1)}
+    out["cost_cascaded_over_rawmrt_f32"] = round(out["rawmrt_f32"]["mlups"] / out["cascaded_f32"]["mlups"] - 1, 4)
+    out["cost_note"] = "paper (Sec. V): cascaded about 11.6 % slower than raw MRT, CPU, hardware not stated"
+    return out
+
+
+def run_e2e(args, lbm, torch, np, n, rho_h, u_h, sp, nodes):
+    """The user's call sequence with host buffers: lbm_init from pinned host
+    (rho, u), lbm_step(inner), lbm_macros into pinned host (rho, u)."""
+    inner = 100
+    iters = max(3, min(20, args.steps // inner))
+    rho_p = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    u_p = torch.empty((2, n, n), dtype=torch.float64, pin_memory=True)
+    rho_p.numpy()[...] = rho_h
+    u_p.numpy()[...] = u_h
+    out_r = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    out_u = torch.empty((2, n, n), dtype=torch.float64, pin_memory=True)
+    L = lbm.Lattice(n, n, omegas(), store=lbm.F32, stream=sp)
+    lib = lbm.load_library()
+
+    def job():
+        lbm._check(lib.lbm_init(L.h, rho_p.data_ptr(), u_p.data_ptr()))
+        lbm.lbm_step(L.h, inner)
+        lbm._check(lib.lbm_macros(L.h, out_r.data_ptr(), out_u.data_ptr()))
+
+    job()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        job()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    L.close()
+    assert np.isfinite(out_u.numpy()).all()
+    return {"value": round(nodes * inner * iters / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": 3 * 8 * nodes // inner, "d2h_bytes_per_step": 3 * 8 * nodes // inner,
+            "steps_per_transfer": inner,
+            "sequence": "lbm_init(pinned host rho,u) + lbm_step(100) + lbm_macros(pinned host rho,u)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

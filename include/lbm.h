@@ -1,0 +1,172 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) cascaded lattice Boltzmann library.
+ *
+ * The library advances a two-dimensional D2Q9 lattice with the cascaded
+ * (central-moment MRT) collision of Ning & Premnath, Sec. II, Eq. (13)-(28),
+ * or with one of the two sibling collisions the paper compares it with
+ * (SRT-BGK and raw-moment MRT, Sec. IV-V).  One call to lbm_step performs
+ * collide-and-stream (Eq. 24-25) at every node in one fused CUDA kernel.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: LBM_OK (0) or one of the LBM_E*
+ *     codes below; lbm_last_error() then gives a one-line message (per host
+ *     thread).  No function aborts or prints.
+ *   - Fields passed in or out are row-major with x fastest: a scalar field is
+ *     [ny][nx], a vector field [2][ny][nx] (x component first), populations
+ *     [9][ny][nx] in the paper's direction order (Eq. 1):
+ *     e = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *   - Lattice units: node spacing 1, time step 1, c_s^2 = 1/3.  Node (i, j)
+ *     sits at x = i, y = j; half-way bounce-back walls sit half a link outside
+ *     the first and last nodes.
+ *   - "host" pointers are ordinary (pageable or pinned) CPU memory; the call
+ *     copies through a stream-ordered device buffer and returns after the copy
+ *     has completed.  "device" pointers are CUDA device memory of the device
+ *     that was current at lbm_create; those calls are asynchronous on the
+ *     handle's stream.
+ *   - A handle is used by one host thread at a time.  The library owns the
+ *     device memory it allocates; lbm_destroy releases it.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL 1    /* an argument is out of range or inconsistent */
+#define LBM_ENOMEM 2    /* a device allocation failed */
+#define LBM_ECUDA 3     /* a CUDA runtime call or kernel launch failed */
+#define LBM_EDIVERGED 4 /* the divergence check found a non-finite or drifting state */
+
+/* edge kinds, one per edge in the order west, east, south, north */
+#define LBM_PERIODIC 0
+#define LBM_BOUNCEBACK 1   /* half-way bounce-back, wall at rest (Sec. III-A) */
+#define LBM_MOVING_WALL 2  /* half-way bounce-back with the moving-wall correction (Sec. III-C) */
+#define LBM_WEST 0
+#define LBM_EAST 1
+#define LBM_SOUTH 2
+#define LBM_NORTH 3
+
+/* collision models */
+#define LBM_CASCADED 0 /* central-moment cascaded collision, Sec. II Eq. (13)-(26) */
+#define LBM_BGK 1      /* single relaxation time, rate omega_4 (named in Sec. I, V) */
+#define LBM_RAWMRT 2   /* raw-moment MRT in the basis K of Eq. (3) (named in Sec. IV-V) */
+
+/* population storage; arithmetic is FP64 for LBM_F64 and FP32 otherwise.
+ * The stored quantity is the deviation f_a - w_a rho0 (w = 4/9, 1/9, 1/36). */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_BF16DEV 2 /* bfloat16, round to nearest even */
+#define LBM_F16DEV 3  /* IEEE half of 4096 * deviation, round to nearest even */
+
+/* boundary specification: edge[k] is the kind of edge k (W, E, S, N);
+ * wall_u[k] the tangential speed of a moving wall (along x on the south and
+ * north edges, along y on the west and east edges; ignored otherwise).
+ * Opposite edges must both be periodic or both be walls. */
+typedef struct {
+    int edge[4];
+    double wall_u[4];
+} lbm_bc_t;
+
+typedef struct lbm_s* lbm_t;
+
+/* Create a lattice of nx x ny nodes on the current CUDA device.
+ *   omegas  : relaxation rates omega_3..omega_8, each in (0, 2) (Sec. II,
+ *             after Eq. 23); omega_4 = omega_5 set the shear viscosity
+ *             nu = (1/omega_4 - 1/2)/3.  BGK uses omega_4 only.
+ *   force   : uniform body force (F_x, F_y) of Eq. (5); NULL means zero.
+ *   bc      : edges; NULL means periodic on all four edges.
+ *   model   : LBM_CASCADED, LBM_BGK or LBM_RAWMRT.
+ *   store   : LBM_F64, LBM_F32, LBM_BF16DEV or LBM_F16DEV.
+ *   rho0    : reference density (> 0): the deviation origin and the density
+ *             used in the moving-wall correction.
+ * The populations start at rest, f = w rho0.  Allocates 9*pitch*ny*sizeof(store)
+ * bytes of device memory (pitch = nx rounded up to 32).
+ * Errors: LBM_EINVAL (nx, ny < 1, ny > 65535 or nx*ny > 2^31 - 1; an omega outside (0,2);
+ * unknown model, store or edge kind; mismatched periodic edges; rho0 <= 0;
+ * out == NULL), LBM_ENOMEM, LBM_ECUDA.  *out is set only on success. */
+int lbm_create(int nx, int ny, const double omegas[6], const double force[2], const lbm_bc_t* bc,
+               int model, int store, double rho0, lbm_t* out);
+
+/* Release the handle and its device memory (after the handle's stream has
+ * drained).  lbm_destroy(NULL) is a no-op returning LBM_OK. */
+int lbm_destroy(lbm_t h);
+
+/* Launch all later work on this CUDA stream (a cudaStream_t; NULL is the
+ * legacy default stream). */
+int lbm_set_stream(lbm_t h, void* stream);
+
+/* Replace the uniform body force (Eq. 5). */
+int lbm_set_force(lbm_t h, const double force[2]);
+
+/* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
+ * on_device selects a device or a host pointer.  The library keeps its own
+ * copy (FP64 for LBM_F64 storage, FP32 otherwise). */
+int lbm_set_force_field(lbm_t h, const double* fxy, int on_device);
+
+/* Set the populations to the equilibrium of the lattice's model at the given
+ * density and velocity, in the transformed variable of Eq. (6):
+ * f_bar = f_eq(rho, u) - S(u, F)/2, so that Eq. (27)-(28) return exactly
+ * (rho, u).  The cascaded model uses the equilibrium whose central moments are
+ * those of Eq. (11); BGK and raw MRT the second-order polynomial one.
+ * rho [ny][nx] may be NULL (rho0 everywhere), u [2][ny][nx] may be NULL (rest).
+ * Resets the step counter to 0.  _device: device pointers. */
+int lbm_init(lbm_t h, const double* rho, const double* u);
+int lbm_init_device(lbm_t h, const double* rho, const double* u);
+
+/* Advance n >= 0 time steps (collide Eq. 24 + stream Eq. 25 per step), one
+ * fused kernel launch per step, asynchronously on the handle's stream.  With
+ * the divergence check on (lbm_set_check) the call synchronises at every
+ * check and returns LBM_EDIVERGED when it fails. */
+int lbm_step(lbm_t h, long n);
+
+/* Density [ny][nx] and velocity [2][ny][nx] of Eq. (27)-(28) at the current
+ * time; either pointer may be NULL.  Host pointers: synchronous. */
+int lbm_macros(lbm_t h, double* rho, double* u);
+int lbm_macros_device(lbm_t h, double* rho, double* u);
+
+/* Local strain-rate quantities from the non-equilibrium moments of
+ * f = f_bar + S/2, Eq. (29)-(31) solved exactly for the two normal
+ * components: out [3][ny][nx] = (d_x j_x, d_y j_y, d_x j_y + d_y j_x). */
+int lbm_strain(lbm_t h, double* out);
+int lbm_strain_device(lbm_t h, double* out);
+
+/* Read or overwrite the populations f_bar [9][ny][nx] (FP64, full values,
+ * not deviations) at the current time.  lbm_set_f resets the step counter to 0. */
+int lbm_get_f(lbm_t h, double* f);
+int lbm_set_f(lbm_t h, const double* f);
+int lbm_get_f_device(lbm_t h, double* f);
+int lbm_set_f_device(lbm_t h, const double* f);
+
+/* Global sums in FP64 over all nodes: out = (sum rho, sum rho u_x, sum rho u_y)
+ * with rho u from Eq. (28).  Synchronous; out is host memory. */
+int lbm_stats(lbm_t h, double out[3]);
+
+/* Divergence check: every `every` steps (0 = off) lbm_step computes
+ * lbm_stats and fails with LBM_EDIVERGED if a sum is not finite or the mass
+ * drifts from its value at the last init by more than mass_rtol (relative). */
+int lbm_set_check(lbm_t h, long every, double mass_rtol);
+
+/* Number of steps taken since create / init / set_f. */
+long lbm_time(lbm_t h);
+
+/* Layout facts: dims = (nx, ny, pitch, model, store); bytes = device bytes of
+ * the population array; state = its device address (for profiling tools). */
+int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state);
+
+/* Algorithmic bytes one lattice update moves for a storage kind: 9 loads and
+ * 9 stores of the stored type (144, 72, 36, 36); 0 for an unknown kind. */
+size_t lbm_bytes_per_update(int store);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

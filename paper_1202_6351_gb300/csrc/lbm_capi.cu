@@ -1,0 +1,450 @@
+// lbm_capi.cu -- the extern "C" boundary declared in include/lbm.h.
+//
+// Validates arguments, owns the device memory of a lattice, tracks the step
+// counter (whose parity selects the AA-pattern kernel) and turns CUDA failures
+// into status codes with a per-thread message.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::Args;
+
+struct lbm_s {
+    int device = 0;
+    Args a{};
+    int model = 0, store = 0;
+    int edge[4] = {0, 0, 0, 0};
+    double wall_u[4] = {0, 0, 0, 0};
+    bool walls = false;
+    bool has_field = false;
+    long t = 0;
+    cudaStream_t stream = nullptr;
+    void* state = nullptr;
+    size_t state_bytes = 0;
+    void* ffield = nullptr;
+    double* partials = nullptr;  // [3 * stats_blocks] FP64 scratch of lbm_stats
+    double* sums = nullptr;      // [3] device result of lbm_stats
+    long check_every = 0;
+    double check_rtol = 0.0, mass0 = 0.0;
+};
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, what)                              \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_size(int store) {
+    switch (store) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        case LBM_BF16DEV:
+        case LBM_F16DEV: return 2;
+        default: return 0;
+    }
+}
+
+int force_mode(const lbm_s* h) {
+    if (h->has_field) return 2;
+    return (h->a.F[0] != 0.0 || h->a.F[1] != 0.0) ? 1 : 0;
+}
+
+cudaError_t launch_step(lbm_s* h, bool odd) {
+    const int fm = force_mode(h);
+    switch (h->store) {
+        case LBM_F64: return lbm::launch_step_f64(h->a, h->model, odd, fm, h->walls, h->stream);
+        case LBM_F32: return lbm::launch_step_f32(h->a, h->model, odd, fm, h->walls, h->stream);
+        case LBM_BF16DEV: return lbm::launch_step_bf16(h->a, h->model, odd, fm, h->walls, h->stream);
+        default: return lbm::launch_step_f16(h->a, h->model, odd, fm, h->walls, h->stream);
+    }
+}
+
+long long nodes(const lbm_s* h) { return (long long)h->a.nx * h->a.ny; }
+
+// Stream-ordered temporary device buffer for host-pointer calls.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t s;
+    explicit DevBuf(cudaStream_t st) : s(st) {}
+    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
+};
+
+int stats_into(lbm_s* h, double out[3]) {
+    LBM_CUDA(lbm::launch_stats(h->a, h->store, h->t & 1, h->walls, force_mode(h), h->partials, h->sums, h->stream),
+             "stats kernel");
+    LBM_CUDA(cudaMemcpyAsync(out, h->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "stats copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
+    return LBM_OK;
+}
+
+int after_reset(lbm_s* h) {
+    h->t = 0;
+    if (h->check_every > 0) {
+        double s[3];
+        int rc = stats_into(h, s);
+        if (rc) return rc;
+        h->mass0 = s[0];
+    }
+    return LBM_OK;
+}
+
+#define CHECK_HANDLE(h)                                              \
+    if (!(h)) return fail(LBM_EINVAL, "null lattice handle");        \
+    DeviceGuard guard_((h)->device);                                 \
+    if (!guard_.ok) return fail(LBM_ECUDA, "cannot select the lattice's device");
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_error.c_str(); }
+
+size_t lbm_bytes_per_update(int store) { return 18 * elem_size(store); }
+
+int lbm_create(int nx, int ny, const double omegas[6], const double force[2], const lbm_bc_t* bc, int model,
+               int store, double rho0, lbm_t* out) {
+    g_error.clear();
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    if (nx < 1 || ny < 1) return fail(LBM_EINVAL, "nx and ny must be >= 1 (got %d x %d)", nx, ny);
+    if ((long long)nx * ny > 0x7fffffffLL) return fail(LBM_EINVAL, "nx * ny exceeds 2^31 - 1");
+    if (ny > 65535) return fail(LBM_EINVAL, "ny = %d exceeds 65535", ny);
+    if (!omegas) return fail(LBM_EINVAL, "omegas is NULL");
+    for (int k = 0; k < 6; ++k)
+        if (!(omegas[k] > 0.0 && omegas[k] < 2.0))
+            return fail(LBM_EINVAL, "omega_%d = %g is outside (0, 2)", k + 3, omegas[k]);
+    if (model < LBM_CASCADED || model > LBM_RAWMRT) return fail(LBM_EINVAL, "unknown model %d", model);
+    if (elem_size(store) == 0) return fail(LBM_EINVAL, "unknown storage kind %d", store);
+    if (!(rho0 > 0.0 && std::isfinite(rho0))) return fail(LBM_EINVAL, "rho0 must be positive and finite");
+    if (force && !(std::isfinite(force[0]) && std::isfinite(force[1])))
+        return fail(LBM_EINVAL, "force must be finite");
+    int edge[4] = {LBM_PERIODIC, LBM_PERIODIC, LBM_PERIODIC, LBM_PERIODIC};
+    double wall_u[4] = {0, 0, 0, 0};
+    if (bc) {
+        for (int k = 0; k < 4; ++k) {
+            if (bc->edge[k] < LBM_PERIODIC || bc->edge[k] > LBM_MOVING_WALL)
+                return fail(LBM_EINVAL, "unknown edge kind %d on edge %d", bc->edge[k], k);
+            if (!std::isfinite(bc->wall_u[k])) return fail(LBM_EINVAL, "wall speed on edge %d is not finite", k);
+            edge[k] = bc->edge[k];
+            wall_u[k] = bc->wall_u[k];
+        }
+        if ((edge[LBM_WEST] == LBM_PERIODIC) != (edge[LBM_EAST] == LBM_PERIODIC))
+            return fail(LBM_EINVAL, "west and east edges must both be periodic or both be walls");
+        if ((edge[LBM_SOUTH] == LBM_PERIODIC) != (edge[LBM_NORTH] == LBM_PERIODIC))
+            return fail(LBM_EINVAL, "south and north edges must both be periodic or both be walls");
+    }
+
+    lbm_s* h = new lbm_s;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(LBM_ECUDA, "no CUDA device available");
+    }
+    h->model = model;
+    h->store = store;
+    Args& a = h->a;
+    a.nx = nx;
+    a.ny = ny;
+    a.pitch = (nx + 31) / 32 * 32;
+    a.plane = (long long)a.pitch * ny;
+    for (int k = 0; k < 6; ++k) a.om[k] = omegas[k];
+    a.F[0] = force ? force[0] : 0.0;
+    a.F[1] = force ? force[1] : 0.0;
+    a.rho0 = rho0;
+    a.ffield = nullptr;
+    for (int k = 0; k < 4; ++k) {
+        h->edge[k] = edge[k];
+        h->wall_u[k] = wall_u[k];
+        a.wall[k] = edge[k] != LBM_PERIODIC;
+        const double U = edge[k] == LBM_MOVING_WALL ? wall_u[k] : 0.0;
+        a.wallx[k] = k >= LBM_SOUTH ? 6.0 * rho0 * U : 0.0;
+        a.wally[k] = k >= LBM_SOUTH ? 0.0 : 6.0 * rho0 * U;
+        h->walls = h->walls || a.wall[k];
+    }
+    lbm::prepare_constants(a);
+    h->state_bytes = 9 * (size_t)a.plane * elem_size(store);
+    cudaError_t e = cudaMalloc(&h->state, h->state_bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->state, 0, h->state_bytes);  // deviation 0: the rest state w rho0
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, (3 * (size_t)lbm::stats_blocks(a) + 3) * sizeof(double));
+    if (e == cudaSuccess) {
+        h->sums = h->partials + 3 * (size_t)lbm::stats_blocks(a);
+        e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "lbm_create");
+        if (h->state) cudaFree(h->state);
+        if (h->partials) cudaFree(h->partials);
+        delete h;
+        return rc;
+    }
+    a.f = h->state;
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_t h) {
+    if (!h) return LBM_OK;
+    int rc = LBM_OK;
+    {
+        DeviceGuard g(h->device);
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+        if (h->state) cudaFree(h->state);
+        if (h->ffield) cudaFree(h->ffield);
+        if (h->partials) cudaFree(h->partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_destroy");
+    }
+    delete h;
+    return rc;
+}
+
+int lbm_set_stream(lbm_t h, void* stream) {
+    CHECK_HANDLE(h);
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_t h, const double force[2]) {
+    CHECK_HANDLE(h);
+    if (!force || !std::isfinite(force[0]) || !std::isfinite(force[1]))
+        return fail(LBM_EINVAL, "force must be two finite numbers");
+    h->a.F[0] = force[0];
+    h->a.F[1] = force[1];
+    lbm::prepare_constants(h->a);
+    return LBM_OK;
+}
+
+int lbm_set_force_field(lbm_t h, const double* fxy, int on_device) {
+    CHECK_HANDLE(h);
+    if (!fxy) {
+        h->has_field = false;
+        h->a.ffield = nullptr;
+        return LBM_OK;
+    }
+    const size_t n = 2 * (size_t)nodes(h);
+    const bool dbl = h->store == LBM_F64;
+    if (!h->ffield) LBM_CUDA(cudaMalloc(&h->ffield, n * (dbl ? 8 : 4)), "force field allocation");
+    DevBuf tmp(h->stream);
+    const double* src = fxy;
+    if (!on_device) {
+        LBM_CUDA(tmp.alloc(n * sizeof(double)), "force field staging");
+        LBM_CUDA(cudaMemcpyAsync(tmp.p, fxy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "force copy");
+        src = static_cast<const double*>(tmp.p);
+    }
+    if (dbl) {
+        LBM_CUDA(cudaMemcpyAsync(h->ffield, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream),
+                 "force copy");
+    } else {
+        // FP32 arithmetic kernels read the field in FP32
+        LBM_CUDA(lbm::launch_narrow(src, static_cast<float*>(h->ffield), n, h->stream), "force narrowing");
+    }
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "force field sync");
+    h->has_field = true;
+    h->a.ffield = h->ffield;
+    return LBM_OK;
+}
+
+static int init_common(lbm_t h, const double* rho, const double* u) {
+    LBM_CUDA(lbm::launch_init(h->a, h->store, h->model, force_mode(h), rho, u, h->stream), "init kernel");
+    return LBM_OK;
+}
+
+int lbm_init_device(lbm_t h, const double* rho, const double* u) {
+    CHECK_HANDLE(h);
+    int rc = init_common(h, rho, u);
+    if (rc) return rc;
+    return after_reset(h);
+}
+
+int lbm_init(lbm_t h, const double* rho, const double* u) {
+    CHECK_HANDLE(h);
+    const size_t n = (size_t)nodes(h);
+    DevBuf buf(h->stream);
+    double* drho = nullptr;
+    double* du = nullptr;
+    if (rho || u) {
+        LBM_CUDA(buf.alloc(3 * n * sizeof(double)), "init staging");
+        drho = static_cast<double*>(buf.p);
+        du = drho + n;
+        if (rho) LBM_CUDA(cudaMemcpyAsync(drho, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "rho copy");
+        if (u) LBM_CUDA(cudaMemcpyAsync(du, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "u copy");
+    }
+    int rc = init_common(h, rho ? drho : nullptr, u ? du : nullptr);
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "init sync");
+    return after_reset(h);
+}
+
+int lbm_step(lbm_t h, long n) {
+    CHECK_HANDLE(h);
+    if (n < 0) return fail(LBM_EINVAL, "step count must be >= 0");
+    for (long s = 0; s < n; ++s) {
+        LBM_CUDA(launch_step(h, (h->t & 1) != 0), "step kernel launch");
+        ++h->t;
+        if (h->check_every > 0 && h->t % h->check_every == 0) {
+            double st[3];
+            int rc = stats_into(h, st);
+            if (rc) return rc;
+            const bool finite = std::isfinite(st[0]) && std::isfinite(st[1]) && std::isfinite(st[2]);
+            if (!finite || std::fabs(st[0] - h->mass0) > h->check_rtol * std::fabs(h->mass0))
+                return fail(LBM_EDIVERGED, "diverged at step %ld: mass %.17g (start %.17g), momentum (%g, %g)", h->t,
+                            st[0], h->mass0, st[1], st[2]);
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_macros_device(lbm_t h, double* rho, double* u) {
+    CHECK_HANDLE(h);
+    LBM_CUDA(lbm::launch_macros(h->a, h->store, h->t & 1, h->walls, force_mode(h), rho, u, h->stream),
+             "macros kernel");
+    return LBM_OK;
+}
+
+int lbm_macros(lbm_t h, double* rho, double* u) {
+    CHECK_HANDLE(h);
+    if (!rho && !u) return LBM_OK;
+    const size_t n = (size_t)nodes(h);
+    DevBuf buf(h->stream);
+    LBM_CUDA(buf.alloc(3 * n * sizeof(double)), "macros staging");
+    double* drho = static_cast<double*>(buf.p);
+    double* du = drho + n;
+    LBM_CUDA(lbm::launch_macros(h->a, h->store, h->t & 1, h->walls, force_mode(h), rho ? drho : nullptr,
+                                u ? du : nullptr, h->stream),
+             "macros kernel");
+    if (rho) LBM_CUDA(cudaMemcpyAsync(rho, drho, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "rho copy");
+    if (u) LBM_CUDA(cudaMemcpyAsync(u, du, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "u copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "macros sync");
+    return LBM_OK;
+}
+
+int lbm_strain_device(lbm_t h, double* out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    LBM_CUDA(lbm::launch_strain(h->a, h->store, h->t & 1, h->walls, force_mode(h), out, h->stream), "strain kernel");
+    return LBM_OK;
+}
+
+int lbm_strain(lbm_t h, double* out) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    const size_t n = 3 * (size_t)nodes(h);
+    DevBuf buf(h->stream);
+    LBM_CUDA(buf.alloc(n * sizeof(double)), "strain staging");
+    LBM_CUDA(lbm::launch_strain(h->a, h->store, h->t & 1, h->walls, force_mode(h), static_cast<double*>(buf.p),
+                                h->stream),
+             "strain kernel");
+    LBM_CUDA(cudaMemcpyAsync(out, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "strain copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "strain sync");
+    return LBM_OK;
+}
+
+int lbm_get_f_device(lbm_t h, double* f) {
+    CHECK_HANDLE(h);
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    LBM_CUDA(lbm::launch_get_f(h->a, h->store, h->t & 1, h->walls, f, h->stream), "get_f kernel");
+    return LBM_OK;
+}
+
+int lbm_get_f(lbm_t h, double* f) {
+    CHECK_HANDLE(h);
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    const size_t n = 9 * (size_t)nodes(h);
+    DevBuf buf(h->stream);
+    LBM_CUDA(buf.alloc(n * sizeof(double)), "get_f staging");
+    LBM_CUDA(lbm::launch_get_f(h->a, h->store, h->t & 1, h->walls, static_cast<double*>(buf.p), h->stream),
+             "get_f kernel");
+    LBM_CUDA(cudaMemcpyAsync(f, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "f copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "get_f sync");
+    return LBM_OK;
+}
+
+int lbm_set_f_device(lbm_t h, const double* f) {
+    CHECK_HANDLE(h);
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    LBM_CUDA(lbm::launch_set_f(h->a, h->store, f, h->stream), "set_f kernel");
+    return after_reset(h);
+}
+
+int lbm_set_f(lbm_t h, const double* f) {
+    CHECK_HANDLE(h);
+    if (!f) return fail(LBM_EINVAL, "f is NULL");
+    const size_t n = 9 * (size_t)nodes(h);
+    DevBuf buf(h->stream);
+    LBM_CUDA(buf.alloc(n * sizeof(double)), "set_f staging");
+    LBM_CUDA(cudaMemcpyAsync(buf.p, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "f copy");
+    LBM_CUDA(lbm::launch_set_f(h->a, h->store, static_cast<const double*>(buf.p), h->stream), "set_f kernel");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "set_f sync");
+    return after_reset(h);
+}
+
+int lbm_stats(lbm_t h, double out[3]) {
+    CHECK_HANDLE(h);
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    return stats_into(h, out);
+}
+
+int lbm_set_check(lbm_t h, long every, double mass_rtol) {
+    CHECK_HANDLE(h);
+    if (every < 0 || !(mass_rtol >= 0.0)) return fail(LBM_EINVAL, "every must be >= 0 and mass_rtol >= 0");
+    h->check_every = every;
+    h->check_rtol = mass_rtol;
+    if (every > 0) {
+        double s[3];
+        int rc = stats_into(h, s);
+        if (rc) return rc;
+        h->mass0 = s[0];
+    }
+    return LBM_OK;
+}
+
+long lbm_time(lbm_t h) { return h ? h->t : -1; }
+
+int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state) {
+    if (!h) return fail(LBM_EINVAL, "null lattice handle");
+    if (dims) {
+        dims[0] = h->a.nx; dims[1] = h->a.ny; dims[2] = h->a.pitch; dims[3] = h->model; dims[4] = h->store;
+    }
+    if (bytes) *bytes = h->state_bytes;
+    if (state) *state = h->state;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// lbm_device.cuh -- device-side building blocks of the fused D2Q9 update.
+//
+// Everything here runs per node in registers: the nine populations of a node
+// are loaded (AA pattern, see below), collided with the cascaded central-moment
+// operator of Sec. II (or a sibling), and stored back.  No tensor cores: the
+// per-node map is a handful of signed sums and FMAs, not a dense contraction.
+//
+// Populations are held as deviations d_a = f_a - w_a rho0 (w = 4/9, 1/9, 1/36),
+// so that the O(1) rest state never enters an FP32 subtraction; the moments of
+// w_a rho0 are added back analytically (sum w = 1, sum w e_x^2 = 1/3,
+// sum w e_x^2 e_y^2 = 1/9, odd moments 0).
+//
+// AA-pattern streaming on one array f[9][ny][pitch] (Bailey et al. layout):
+//   even step: node x reads slot a of x and writes its post-collision a into
+//              slot abar of x (no neighbour access);
+//   odd step:  node x reads slot abar of x - e_a (the value the neighbour
+//              stored there at the even step) and writes post-collision a into
+//              slot a of x + e_a.
+// Every slot is read and written by one thread only, so the update is in
+// place.  After an even number of steps slot a of node x holds f_a(x).
+// Half-way bounce-back: a link whose far end lies beyond a wall is reflected
+// at the node itself, with the moving-wall term 6 w_a rho_w (e_a . U_wall)
+// (Sec. III-C); a link leaving through a south/north wall is decided by that
+// wall even when it also leaves in x.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattice
+__host__ __device__ constexpr int cx(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : (a == 3 || a == 6 || a == 7) ? -1 : 0; }
+__host__ __device__ constexpr int cy(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0; }
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : (a < 5 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5); }
+template <typename R>
+__host__ __device__ constexpr R wgt(int a) { return a == 0 ? R(4) / R(9) : (a < 5 ? R(1) / R(9) : R(1) / R(36)); }
+
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opposites");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opposites");
+
+// ---------------------------------------------------------------- storage
+template <int STORE> struct Store;
+template <> struct Store<LBM_F64> {
+    using T = double; using R = double;
+    static __device__ __forceinline__ R dec(T v) { return v; }
+    static __device__ __forceinline__ T enc(R v) { return v; }
+};
+template <> struct Store<LBM_F32> {
+    using T = float; using R = float;
+    static __device__ __forceinline__ R dec(T v) { return v; }
+    static __device__ __forceinline__ T enc(R v) { return v; }
+};
+template <> struct Store<LBM_BF16DEV> {
+    using T = __nv_bfloat16; using R = float;
+    static __device__ __forceinline__ R dec(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ T enc(R v) { return __float2bfloat16_rn(v); }
+};
+// FP16 keeps 4096 x deviation: deviations of 1.5e-8 .. 16 stay normal numbers.
+constexpr float kF16Scale = 4096.0f;
+template <> struct Store<LBM_F16DEV> {
+    using T = __half; using R = float;
+    static __device__ __forceinline__ R dec(T v) { return __half2float(v) * (1.0f / kF16Scale); }
+    static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v * kF16Scale); }
+};
+
+// ---------------------------------------------------------------- launch arguments
+// Plain-old-data, passed by value to every kernel.
+// Index of the per-launch constants in Args::kf / Args::kd.
+enum : int { K_C3 = 0, K_W3 = 6, K_RHO0 = 12, K_FX = 13, K_FY = 14, K_COUNT = 16 };
+
+struct Args {
+    void* f;                  // populations [9][ny][pitch] of the stored type
+    long long plane;          // pitch * ny
+    int nx, ny, pitch;
+    int wall[4];              // 1 if the edge (W, E, S, N) is a wall
+    double wallx[4], wally[4];// 6 rho_w U_wall (x, y components) per edge
+    double om[6];             // omega_3 .. omega_8
+    double F[2];              // uniform body force
+    const void* ffield;       // per-node force [2][ny][nx] (Real), or null
+    double rho0;
+    // The constants the kernels use, converted once on the host into both
+    // arithmetic types (GB300's FP64 rate is far too low for per-thread
+    // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 18-23),
+    // omega_3 .. omega_8, rho0, F_x, F_y; and the wall terms in FP32.
+    float kf[K_COUNT];
+    double kd[K_COUNT];
+    float wallxf[4], wallyf[4];
+};
+
+// Fill Args::kf, kd, wallxf, wallyf from om, rho0, F, wallx, wally.
+inline void prepare_constants(Args& a) {
+    a.kd[K_C3] = a.om[0] / 12.0;
+    for (int k = 1; k < 6; ++k) a.kd[K_C3 + k] = a.om[k] / 4.0;
+    for (int k = 0; k < 6; ++k) a.kd[K_W3 + k] = a.om[k];
+    a.kd[K_RHO0] = a.rho0;
+    a.kd[K_FX] = a.F[0];
+    a.kd[K_FY] = a.F[1];
+    a.kd[15] = 0.0;
+    for (int k = 0; k < K_COUNT; ++k) a.kf[k] = float(a.kd[k]);
+    for (int k = 0; k < 4; ++k) { a.wallxf[k] = float(a.wallx[k]); a.wallyf[k] = float(a.wally[k]); }
+}
+
+template <typename R> __device__ __forceinline__ const R* kconst(const Args& a);
+template <> __device__ __forceinline__ const float* kconst<float>(const Args& a) { return a.kf; }
+template <> __device__ __forceinline__ const double* kconst<double>(const Args& a) { return a.kd; }
+
+// Relaxation constants in the arithmetic type.
+template <typename R>
+struct Coef {
+    R c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, ..., omega_8/4 (Eq. 18-23)
+    R w3, w4, w5, w6, w7, w8;  // the rates themselves (MRT, BGK)
+    R rho0;
+    __device__ __forceinline__ explicit Coef(const Args& a) {
+        const R* k = kconst<R>(a);
+        c3 = k[K_C3]; c4 = k[K_C3 + 1]; c5 = k[K_C3 + 2]; c6 = k[K_C3 + 3]; c7 = k[K_C3 + 4]; c8 = k[K_C3 + 5];
+        w3 = k[K_W3]; w4 = k[K_W3 + 1]; w5 = k[K_W3 + 2]; w6 = k[K_W3 + 3]; w7 = k[K_W3 + 4]; w8 = k[K_W3 + 5];
+        rho0 = k[K_RHO0];
+    }
+};
+
+// ---------------------------------------------------------------- walls
+// Wall through which the link arriving at (x, y) in direction q comes from
+// outside the lattice, or -1.  South/north first (corner links hit the lid).
+__device__ __forceinline__ int incoming_wall(const Args& a, int q, int x, int y) {
+    if (cy(q) == 1 && y == 0 && a.wall[LBM_SOUTH]) return LBM_SOUTH;
+    if (cy(q) == -1 && y == a.ny - 1 && a.wall[LBM_NORTH]) return LBM_NORTH;
+    if (cx(q) == 1 && x == 0 && a.wall[LBM_WEST]) return LBM_WEST;
+    if (cx(q) == -1 && x == a.nx - 1 && a.wall[LBM_EAST]) return LBM_EAST;
+    return -1;
+}
+// Moving-wall term for a population entering in direction q through wall w.
+template <typename R>
+__device__ __forceinline__ R wall_term(const Args& a, int q, int w) {
+    if constexpr (sizeof(R) == 4) return wgt<R>(q) * (R(cx(q)) * a.wallxf[w] + R(cy(q)) * a.wallyf[w]);
+    else return wgt<R>(q) * (R(cx(q)) * a.wallx[w] + R(cy(q)) * a.wally[w]);
+}
+
+// ---------------------------------------------------------------- AA access
+// Load the nine pre-collision deviations of node (x, y).  ODD selects the
+// parity of the step about to be taken (see the header comment).
+template <int STORE, bool ODD, bool WALLS>
+__device__ __forceinline__ void load_node(const Args& a, int x, int y, typename Store<STORE>::R d[9]) {
+    using S = Store<STORE>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const T* __restrict__ f = static_cast<const T*>(a.f);
+    const long long n = (long long)y * a.pitch + x;
+    if (!ODD) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] = S::dec(f[q * a.plane + n]);
+    } else {
+        const int xm = x > 0 ? x - 1 : a.nx - 1, xp = x < a.nx - 1 ? x + 1 : 0;
+        const int ym = y > 0 ? y - 1 : a.ny - 1, yp = y < a.ny - 1 ? y + 1 : 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            int w = -1;
+            if (WALLS) w = incoming_wall(a, q, x, y);
+            if (w >= 0) {
+                d[q] = S::dec(f[q * a.plane + n]) + wall_term<R>(a, q, w);
+            } else {
+                const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
+                const int sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y);
+                d[q] = S::dec(f[opp(q) * a.plane + (long long)sy * a.pitch + sx]);
+            }
+        }
+    }
+}
+
+// Store the nine post-collision deviations of node (x, y).
+template <int STORE, bool ODD, bool WALLS>
+__device__ __forceinline__ void store_node(const Args& a, int x, int y, const typename Store<STORE>::R d[9]) {
+    using S = Store<STORE>;
+    using T = typename S::T;
+    using R = typename S::R;
+    T* __restrict__ f = static_cast<T*>(a.f);
+    const long long n = (long long)y * a.pitch + x;
+    if (!ODD) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[opp(q) * a.plane + n] = S::enc(d[q]);
+    } else {
+        const int xm = x > 0 ? x - 1 : a.nx - 1, xp = x < a.nx - 1 ? x + 1 : 0;
+        const int ym = y > 0 ? y - 1 : a.ny - 1, yp = y < a.ny - 1 ? y + 1 : 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            int w = -1;
+            if (WALLS) w = incoming_wall(a, opp(q), x, y);
+            if (w >= 0) {
+                f[opp(q) * a.plane + n] = S::enc(d[q] + wall_term<R>(a, opp(q), w));
+            } else {
+                const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);
+                const int ty = cy(q) == 1 ? yp : (cy(q) == -1 ? ym : y);
+                f[q * a.plane + (long long)ty * a.pitch + tx] = S::enc(d[q]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- per-node force
+template <typename R, int FORCE>
+__device__ __forceinline__ void node_force(const Args& a, int x, int y, R& Fx, R& Fy) {
+    if (FORCE == 0) { Fx = R(0); Fy = R(0); return; }
+    Fx = kconst<R>(a)[K_FX]; Fy = kconst<R>(a)[K_FY];
+    if (FORCE == 2) {
+        const R* ff = static_cast<const R*>(a.ffield);
+        const long long n = (long long)y * a.nx + x;
+        Fx += ff[n];
+        Fy += ff[(long long)a.nx * a.ny + n];
+    }
+}
+
+// ---------------------------------------------------------------- moments
+template <typename R>
+struct Moments {
+    R drho, rho, jx, jy;           // sum d, rho0 + drho, sum d e (momentum of f_bar)
+    R kxx, kyy, kxy, kxxy, kxyy, kxxyy;  // raw moments of d (Eq. 16 without the rho0 w part)
+};
+
+template <typename R>
+__device__ __forceinline__ Moments<R> moments(const R d[9], R rho0) {
+    Moments<R> m;
+    const R s13 = d[1] + d[3], s24 = d[2] + d[4];
+    const R s56 = d[5] + d[6], s78 = d[7] + d[8];
+    const R s58 = d[5] + d[8], s67 = d[6] + d[7];
+    m.kxxyy = s56 + s78;
+    m.kxx = s13 + m.kxxyy;
+    m.kyy = s24 + m.kxxyy;
+    m.drho = d[0] + s13 + m.kyy;
+    m.rho = rho0 + m.drho;
+    m.jx = (d[1] - d[3]) + (s58 - s67);
+    m.jy = (d[2] - d[4]) + (s56 - s78);
+    m.kxy = (d[5] + d[7]) - (d[6] + d[8]);
+    m.kxxy = s56 - s78;
+    m.kxyy = s58 - s67;
+    return m;
+}
+
+// Source S_a (Eq. 14-15) for force (Fx, Fy) at velocity (ux, uy).
+template <typename R>
+__device__ __forceinline__ void source(R ux, R uy, R Fx, R Fy, R S[9]) {
+    const R m1 = Fx, m2 = Fy;
+    const R m3 = R(6) * (Fx * ux + Fy * uy);
+    const R m4 = R(2) * (Fx * ux - Fy * uy);
+    const R m5 = Fx * uy + Fy * ux;
+    const R m6 = (R(2) - R(3) * ux * ux) * Fy - R(6) * Fx * ux * uy;
+    const R m7 = (R(2) - R(3) * uy * uy) * Fx - R(6) * Fy * uy * ux;
+    const R m8 = R(6) * ((R(3) * uy * uy - R(2)) * Fx * ux + (R(3) * ux * ux - R(2)) * Fy * uy);
+    const R k = R(1) / R(36);
+    S[0] = k * (R(4) * (m8 - m3));
+    S[1] = k * (R(6) * m1 - m3 + R(9) * m4 + R(6) * m7 - R(2) * m8);
+    S[2] = k * (R(6) * m2 - m3 - R(9) * m4 + R(6) * m6 - R(2) * m8);
+    S[3] = k * (-R(6) * m1 - m3 + R(9) * m4 - R(6) * m7 - R(2) * m8);
+    S[4] = k * (-R(6) * m2 - m3 - R(9) * m4 - R(6) * m6 - R(2) * m8);
+    S[5] = k * (R(6) * (m1 + m2) + R(2) * m3 + R(9) * m5 - R(3) * (m6 + m7) + m8);
+    S[6] = k * (R(6) * (m2 - m1) + R(2) * m3 - R(9) * m5 - R(3) * (m6 - m7) + m8);
+    S[7] = k * (-R(6) * (m1 + m2) + R(2) * m3 + R(9) * m5 + R(3) * (m6 + m7) + m8);
+    S[8] = k * (R(6) * (m1 - m2) + R(2) * m3 - R(9) * m5 + R(3) * (m6 - m7) + m8);
+}
+
+// Add K . g (Eq. 26; g0 = g1 = g2 = 0) to d.
+template <typename R>
+__device__ __forceinline__ void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
+    const R t = R(2) * g3 + g8;
+    const R a = g4 - g3;             // f1, f3 share -g3 + g4
+    const R b = -g3 - g4;            // f2, f4 share -g3 - g4
+    d[0] += R(4) * (g8 - g3);
+    d[1] += a + R(2) * (g7 - g8);
+    d[3] += a - R(2) * (g7 + g8);
+    d[2] += b + R(2) * (g6 - g8);
+    d[4] += b - R(2) * (g6 + g8);
+    const R p = g5 - g6, q = g5 + g6;
+    d[5] += t + p - g7;
+    d[6] += t - q + g7;
+    d[7] += t + q + g7;
+    d[8] += t - p - g7;
+}
+
+// ---------------------------------------------------------------- cascaded collision
+// Sec. II, Eq. (13)-(26), on deviations.  FORCE = 0: no source terms.
+template <typename R, bool FORCED>
+__device__ __forceinline__ void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
+    const Moments<R> m = moments(d, c.rho0);
+    const R inv = R(1) / m.rho;
+    const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (28)
+    const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
+    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R r3 = c.rho0 * R(1.0 / 3.0);
+    // raw source moments, Eq. (13)
+    R sxx = 0, syy = 0, sxy = 0, sxxy = 0, sxyy = 0, sxxyy = 0;
+    if (FORCED) {
+        sxx = R(2) * Fx * ux; syy = R(2) * Fy * uy; sxy = Fx * uy + Fy * ux;
+        sxxy = Fy * uxx + R(2) * Fx * uxy; sxyy = Fx * uyy + R(2) * Fy * uxy;
+        sxxyy = R(2) * uxy * (Fx * uy + Fy * ux);
+    }
+    const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;  // full kappa'_xx, kappa'_yy
+    // Eq. (18)-(20)
+    const R g3 = c.c3 * (R(2.0 / 3.0) * m.drho + m.rho * (uxx + uyy) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
+    const R g4 = c.c4 * (m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy));
+    const R g5 = c.c5 * (m.rho * uxy - m.kxy - R(0.5) * sxy);
+    const R A = R(3) * g3 + g4, B = R(3) * g3 - g4;
+    // Eq. (21)-(22)
+    const R g6 = c.c6 * (R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy)
+               - R(0.5) * uy * A - R(2) * ux * g5;
+    const R g7 = c.c7 * (R(2) * m.rho * ux * uyy + m.kxyy - R(2) * uy * m.kxy - ux * kyy_t - R(0.5) * sxyy)
+               - R(0.5) * ux * B - R(2) * uy * g5;
+    // Eq. (23)
+    const R g8 = c.c8 * (R(1.0 / 9.0) * m.drho - m.kxxyy + R(3) * m.rho * uxx * uyy
+                         + R(2) * (ux * m.kxyy + uy * m.kxxy) - uxx * kyy_t - uyy * kxx_t
+                         - R(4) * uxy * m.kxy - R(0.5) * sxxyy)
+               - R(2) * g3 - R(0.5) * (uyy * A + uxx * B) - R(4) * uxy * g5 - R(2) * (uy * g6 + ux * g7);
+    add_kernel(d, g3, g4, g5, g6, g7, g8);
+    if (FORCED) {
+        R S[9];
+        source(ux, uy, Fx, Fy, S);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] += S[q];
+    }
+}
+
+// ---------------------------------------------------------------- SRT-BGK sibling
+// d~ = d - w (d - d_eq) + (1 - w/2) S with the 2nd-order polynomial f_eq and w = omega_4.
+template <typename R, bool FORCED>
+__device__ __forceinline__ void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
+    const Moments<R> m = moments(d, c.rho0);
+    const R inv = R(1) / m.rho;
+    const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
+    const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
+    const R usq = R(1.5) * (ux * ux + uy * uy);
+    const R w = c.w4;
+    R S[9];
+    if (FORCED) source(ux, uy, Fx, Fy, S);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
+        const R deq = wgt<R>(q) * (m.drho + m.rho * (R(3) * eu + R(4.5) * eu * eu - usq));
+        d[q] = d[q] - w * (d[q] - deq);
+        if (FORCED) d[q] += (R(1) - R(0.5) * w) * S[q];
+    }
+}
+
+// ---------------------------------------------------------------- raw-moment MRT sibling
+// f~ = f - K D^-1 [L (m - m_eq) - (I - L/2) m_s], L = diag(0,0,0,omega_3..omega_8),
+// basis K of Eq. (3), polynomial equilibrium moments m_eq in closed form.
+template <typename R, bool FORCED>
+__device__ __forceinline__ void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
+    const Moments<R> m = moments(d, c.rho0);
+    const R inv = R(1) / m.rho;
+    const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
+    const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
+    const R uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
+    // orthogonal moments of d (the rest-state part w rho0 is added to m_eq's side)
+    const R tr = m.kxx + m.kyy;
+    const R m3 = R(3) * tr - R(4) * m.drho;
+    const R m4 = m.kxx - m.kyy;
+    const R m5 = m.kxy;
+    const R m6 = R(2) * m.jy - R(3) * m.kxxy;
+    const R m7 = R(2) * m.jx - R(3) * m.kxyy;
+    const R m8 = R(9) * m.kxxyy - R(6) * tr + R(4) * m.drho;
+    // equilibrium moments of f_eq - w rho0
+    const R e3 = R(3) * m.rho * usq - R(2) * m.drho;
+    const R e4 = m.rho * (uxx - uyy);
+    const R e5 = m.rho * ux * uy;
+    const R e6 = m.rho * uy;
+    const R e7 = m.rho * ux;
+    const R e8 = m.drho - R(3) * m.rho * usq;
+    R s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0, s8 = 0;
+    if (FORCED) {  // Eq. (14)
+        s3 = R(6) * (Fx * ux + Fy * uy); s4 = R(2) * (Fx * ux - Fy * uy); s5 = Fx * uy + Fy * ux;
+        s6 = (R(2) - R(3) * uxx) * Fy - R(6) * Fx * ux * uy;
+        s7 = (R(2) - R(3) * uyy) * Fx - R(6) * Fy * uy * ux;
+        s8 = R(6) * ((R(3) * uyy - R(2)) * Fx * ux + (R(3) * uxx - R(2)) * Fy * uy);
+    }
+    // change of each orthogonal moment divided by its norm D_b
+    const R g3 = (-c.w3 * (m3 - e3) + (R(1) - R(0.5) * c.w3) * s3) * R(1.0 / 36.0);
+    const R g4 = (-c.w4 * (m4 - e4) + (R(1) - R(0.5) * c.w4) * s4) * R(0.25);
+    const R g5 = (-c.w5 * (m5 - e5) + (R(1) - R(0.5) * c.w5) * s5) * R(0.25);
+    const R g6 = (-c.w6 * (m6 - e6) + (R(1) - R(0.5) * c.w6) * s6) * R(1.0 / 12.0);
+    const R g7 = (-c.w7 * (m7 - e7) + (R(1) - R(0.5) * c.w7) * s7) * R(1.0 / 12.0);
+    const R g8 = (-c.w8 * (m8 - e8) + (R(1) - R(0.5) * c.w8) * s8) * R(1.0 / 36.0);
+    // d += K g over b = 3..8 with columns of Eq. (3), plus the momentum source F/6 on K1, K2
+    R fx6 = 0, fy6 = 0;
+    if (FORCED) { fx6 = Fx * R(1.0 / 6.0); fy6 = Fy * R(1.0 / 6.0); }
+    d[0] += R(-4) * g3 + R(4) * g8;
+    d[1] += fx6 - g3 + g4 + R(2) * g7 - R(2) * g8;
+    d[2] += fy6 - g3 - g4 + R(2) * g6 - R(2) * g8;
+    d[3] += -fx6 - g3 + g4 - R(2) * g7 - R(2) * g8;
+    d[4] += -fy6 - g3 - g4 - R(2) * g6 - R(2) * g8;
+    d[5] += fx6 + fy6 + R(2) * g3 + g5 - g6 - g7 + g8;
+    d[6] += -fx6 + fy6 + R(2) * g3 - g5 - g6 + g7 + g8;
+    d[7] += -fx6 - fy6 + R(2) * g3 + g5 + g6 + g7 + g8;
+    d[8] += fx6 - fy6 + R(2) * g3 - g5 + g6 - g7 + g8;
+}
+
+template <int MODEL, typename R, bool FORCED>
+__device__ __forceinline__ void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
+    if (MODEL == LBM_CASCADED) collide_cascaded<R, FORCED>(d, Fx, Fy, c);
+    else if (MODEL == LBM_BGK) collide_bgk<R, FORCED>(d, Fx, Fy, c);
+    else collide_rawmrt<R, FORCED>(d, Fx, Fy, c);
+}
+
+}  // namespace lbm

@@ -1,0 +1,36 @@
+// lbm_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Launch shape of the fused step kernel: one thread per node, BX x BY threads.
+constexpr int kStepBX = 128;
+constexpr int kStepBY = 2;
+
+// One fused collide-and-stream step (defined once per storage type).
+cudaError_t launch_step_f64(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
+cudaError_t launch_step_f32(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
+cudaError_t launch_step_bf16(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
+cudaError_t launch_step_f16(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
+
+// Auxiliary kernels (lbm_aux.cu); every field argument is dense [..][ny][nx] FP64 device memory.
+cudaError_t launch_init(const Args& a, int store, int model, int force, const double* rho, const double* u,
+                        cudaStream_t s);
+cudaError_t launch_set_f(const Args& a, int store, const double* f, cudaStream_t s);
+cudaError_t launch_get_f(const Args& a, int store, bool odd, bool walls, double* f, cudaStream_t s);
+cudaError_t launch_macros(const Args& a, int store, bool odd, bool walls, int force, double* rho, double* u,
+                          cudaStream_t s);
+cudaError_t launch_strain(const Args& a, int store, bool odd, bool walls, int force, double* out, cudaStream_t s);
+// FP64 sums (rho, rho ux, rho uy) into partials[3 * nblocks] then out[3] (device).
+int stats_blocks(const Args& a);
+cudaError_t launch_stats(const Args& a, int store, bool odd, bool walls, int force, double* partials, double* out,
+                         cudaStream_t s);
+
+// dst[i] = (float)src[i], round to nearest.
+cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,66 @@
+// lbm_step_impl.cuh -- the fused D2Q9 stream-and-collide kernel, instantiated
+// once per storage type by lbm_step_<store>.cu.
+//
+// One thread per node: AA-pattern load of the nine populations (a1, a2),
+// decode to FP32/FP64 deviations (a3), macroscopic fields (a4, Eq. 27-28),
+// raw moments (a5, Eq. 16), source (a6, Eq. 13-15), cascaded kernel g3..g8
+// (a7, Eq. 18-23) or a sibling collision, back-transform (a8, Eq. 26), encode
+// and AA-pattern store (a9).  All of it in registers, one launch per time step.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+__global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
+    using R = typename Store<STORE>::R;
+    const int x = blockIdx.x * kStepBX + threadIdx.x;
+    const int y = blockIdx.y * kStepBY + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    const Coef<R> c(a);
+    R d[9];
+    load_node<STORE, ODD, WALLS>(a, x, y, d);
+    R Fx, Fy;
+    node_force<R, FORCE>(a, x, y, Fx, Fy);
+    collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
+    store_node<STORE, ODD, WALLS>(a, x, y, d);
+}
+
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+static cudaError_t launch_one(const Args& a, cudaStream_t s) {
+    const dim3 block(kStepBX, kStepBY);
+    const dim3 grid((a.nx + kStepBX - 1) / kStepBX, (a.ny + kStepBY - 1) / kStepBY);
+    step_kernel<MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int STORE, bool ODD, int FORCE>
+static cudaError_t pick_walls(const Args& a, bool walls, cudaStream_t s) {
+    return walls ? launch_one<MODEL, STORE, ODD, FORCE, true>(a, s) : launch_one<MODEL, STORE, ODD, FORCE, false>(a, s);
+}
+
+template <int MODEL, int STORE, bool ODD>
+static cudaError_t pick_force(const Args& a, int force, bool walls, cudaStream_t s) {
+    switch (force) {
+        case 0: return pick_walls<MODEL, STORE, ODD, 0>(a, walls, s);
+        case 1: return pick_walls<MODEL, STORE, ODD, 1>(a, walls, s);
+        default: return pick_walls<MODEL, STORE, ODD, 2>(a, walls, s);
+    }
+}
+
+template <int MODEL, int STORE>
+static cudaError_t pick_parity(const Args& a, bool odd, int force, bool walls, cudaStream_t s) {
+    return odd ? pick_force<MODEL, STORE, true>(a, force, walls, s) : pick_force<MODEL, STORE, false>(a, force, walls, s);
+}
+
+template <int STORE>
+static cudaError_t launch_step_store(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s) {
+    switch (model) {
+        case LBM_CASCADED: return pick_parity<LBM_CASCADED, STORE>(a, odd, force, walls, s);
+        case LBM_BGK: return pick_parity<LBM_BGK, STORE>(a, odd, force, walls, s);
+        default: return pick_parity<LBM_RAWMRT, STORE>(a, odd, force, walls, s);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,88 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol that
+include/lbm.h declares, and its host-side argument checks answer correctly.
+No kernel is launched here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1202_6351_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_step", "lbm_macros", "lbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load_library()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(lbm.SIGNATURES)
+
+
+def test_library_is_built_for_sm103a_only():
+    from paper_1202_6351_gb300 import build as B
+
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(lbm.library_path())
+
+
+def test_bytes_per_update():
+    assert [lbm.lbm_bytes_per_update(s) for s in (lbm.F64, lbm.F32, lbm.BF16DEV, lbm.F16DEV)] == [144, 72, 36, 36]
+    assert lbm.lbm_bytes_per_update(99) == 0
+
+
+BAD_CREATE = [
+    dict(nx=0, ny=4),
+    dict(nx=4, ny=-1),
+    dict(nx=70000, ny=70000),
+    dict(omegas=(1.0, 2.0, 1.0, 1.0, 1.0, 1.0)),
+    dict(omegas=(0.0, 1.0, 1.0, 1.0, 1.0, 1.0)),
+    dict(model=7),
+    dict(store=9),
+    dict(rho0=0.0),
+    dict(edges=(lbm.PERIODIC, lbm.BOUNCEBACK, lbm.PERIODIC, lbm.PERIODIC)),
+    dict(edges=(lbm.PERIODIC, lbm.PERIODIC, lbm.MOVING_WALL, lbm.PERIODIC)),
+    dict(edges=(5, 5, 0, 0)),
+    dict(force=(float("nan"), 0.0)),
+]
+
+
+@pytest.mark.parametrize("kw", BAD_CREATE)
+def test_create_rejects_bad_arguments_before_touching_the_device(kw):
+    args = dict(nx=8, ny=8, omegas=(1.0,) * 6)
+    args.update(kw)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_create(**args)
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error()
+
+
+def test_null_handles():
+    lib = lbm.load_library()
+    assert lib.lbm_destroy(None) == lbm.LBM_OK
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_macros(None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_time(None) == -1
+    out = (C.c_double * 3)()
+    assert lib.lbm_stats(None, out) == lbm.LBM_EINVAL

@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: FP64 storage/arithmetic <= 1e-12 relative (max-norm of f) per step and
+<= 1e-10 after 1000 steps; FP32 <= 1e-5 relative L2 velocity error after 1000
+steps; reduced-precision storage within the bounds stated in the test.
+Inputs are seeded; expected values come from the oracle only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1202_6351_gb300 import lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+EDGES = {
+    "periodic": ((lbm.PERIODIC,) * 4, (0, 0, 0, 0)),
+    "channel": ((lbm.PERIODIC, lbm.PERIODIC, lbm.BOUNCEBACK, lbm.BOUNCEBACK), (0, 0, 0, 0)),
+    "ychannel": ((lbm.BOUNCEBACK, lbm.BOUNCEBACK, lbm.PERIODIC, lbm.PERIODIC), (0, 0, 0, 0)),
+    "cavity": ((lbm.BOUNCEBACK, lbm.BOUNCEBACK, lbm.BOUNCEBACK, lbm.MOVING_WALL), (0, 0, 0, 0.1)),
+    "allmoving": ((lbm.MOVING_WALL,) * 4, (0.03, -0.02, 0.05, 0.08)),
+    "couette": ((lbm.PERIODIC, lbm.PERIODIC, lbm.MOVING_WALL, lbm.MOVING_WALL), (0, 0, -0.04, 0.06)),
+}
+MODELS = [lbm.CASCADED, lbm.BGK, lbm.RAWMRT]
+OMEGAS = (1.3, 1.7, 1.6, 0.9, 1.1, 1.2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    lbm.load_library()
+    yield
+
+
+def pair(nx, ny, model=lbm.CASCADED, store=lbm.F64, edges="periodic", omegas=OMEGAS, force=(0.0, 0.0),
+         force_field=None):
+    e, wu = EDGES[edges]
+    gpu = lbm.Lattice(nx, ny, omegas, force=force, edges=e, wall_u=wu, model=model, store=store)
+    if force_field is not None:
+        gpu.set_force_field(force_field)
+    ref = O.Lattice(nx, ny, omegas, force=force, edges=e, wall_u=wu, model=model, force_field=force_field)
+    return gpu, ref
+
+
+def random_state(ref, seed, noise=0.02):
+    rho, u = workloads.random_fields(seed, ref.nx, ref.ny)
+    ref.init(rho, u)
+    ref.f *= 1.0 + workloads.random_noise(seed + 1, ref.f.shape, noise)
+    return ref.f.copy()
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+# ---------------------------------------------------------------- FP64 per-step parity
+
+@pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
+@pytest.mark.parametrize("edges", list(EDGES))
+@pytest.mark.parametrize("forced", [False, True], ids=["unforced", "forced"])
+def test_f64_steps_match_oracle_from_random_state(model, edges, forced):
+    """37 x 23 (ragged against the 128 x 2 block and the 32-wide pitch), random
+    non-equilibrium state; 1, 2 and 3 steps cover both AA parities."""
+    force = (2e-4, -1e-4) if forced else (0.0, 0.0)
+    gpu, ref = pair(37, 23, model, lbm.F64, edges, force=force)
+    f0 = random_state(ref, 100 + model)
+    gpu.set_f(f0)
+    for k in range(3):
+        gpu.step(1)
+        ref.run(1)
+        assert rel_max(gpu.get_f(), ref.f) <= 1e-12, f"step {k + 1}"
+    rho_g, u_g = gpu.macros()
+    rho_r, u_r = ref.macros()
+    assert rel_max(rho_g, rho_r) <= 1e-13
+    assert rel_max(u_g, u_r) <= 1e-11
+    gpu.close()
+
+
+def test_f64_force_field_matches_oracle():
+    ff = workloads.random_force_field(7, 40, 30, 1e-4)
+    for model in MODELS:
+        gpu, ref = pair(40, 30, model, lbm.F64, "channel", force=(1e-5, 0.0), force_field=ff)
+        f0 = random_state(ref, 11)
+        gpu.set_f(f0)
+        gpu.step(5)
+        ref.run(5)
+        assert rel_max(gpu.get_f(), ref.f) <= 1e-12
+        np.testing.assert_allclose(gpu.strain(), ref.strain(), rtol=0, atol=1e-13)
+        gpu.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 1), (1, 33), (3, 5)])
+@pytest.mark.parametrize("edges", ["periodic", "cavity", "allmoving", "channel"])
+def test_f64_degenerate_sizes(shape, edges):
+    nx, ny = shape
+    gpu, ref = pair(nx, ny, lbm.CASCADED, lbm.F64, edges, force=(1e-4, 2e-4))
+    f0 = random_state(ref, 5)
+    gpu.set_f(f0)
+    gpu.step(4)
+    ref.run(4)
+    assert rel_max(gpu.get_f(), ref.f) <= 1e-12
+    gpu.close()
+
+
+def test_f64_taylor_green_1000_steps():
+    n = 64
+    om = 1.6
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    gpu = lbm.Lattice(n, n, oms, store=lbm.F64).init(rho, u)
+    ref = O.Lattice(n, n, oms).init(rho, u)
+    assert rel_max(gpu.get_f(), ref.f) <= 1e-15
+    gpu.step(1000)
+    ref.run(1000)
+    assert rel_max(gpu.get_f(), ref.f) <= 1e-10
+    gpu.close()
+
+
+def test_f64_poiseuille_config_matches_oracle_and_parabola():
+    om = 1 / 0.8
+    nu = O.nu_from_omega(om)
+    fx = 8 * nu * 0.01 / 32 ** 2
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    gpu, ref = pair(4, 32, lbm.CASCADED, lbm.F64, "channel", omegas=oms, force=(fx, 0.0))
+    gpu.init()
+    ref.init()
+    gpu.step(20000)
+    ref.run(20000)
+    assert rel_max(gpu.get_f(), ref.f) <= 1e-12
+    _, u = gpu.macros()
+    ua = O.poiseuille_profile(32, fx, nu)
+    assert np.abs(u[0][:, 0] - ua).max() / ua.max() < 0.0022
+    gpu.close()
+
+
+@pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
+def test_cavity_parity_f64_and_f32(model):
+    n, U, re = 65, 0.1, 400.0
+    nu = U * (n - 1) / re
+    om = O.omega_from_nu(nu)
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    ref = O.Lattice(n, n, oms, edges=EDGES["cavity"][0], wall_u=EDGES["cavity"][1], model=model).init()
+    ref.run(2000)
+    _, u_ref = ref.macros()
+    for store, tol in ((lbm.F64, 1e-10), (lbm.F32, 1e-5)):
+        gpu = lbm.Lattice(n, n, oms, edges=EDGES["cavity"][0], wall_u=EDGES["cavity"][1], model=model,
+                          store=store).init()
+        gpu.step(2000)
+        _, u = gpu.macros()
+        if store == lbm.F64:
+            assert rel_max(gpu.get_f(), ref.f) <= tol
+        else:
+            assert rel_l2(u, u_ref) <= tol
+        gpu.close()
+
+
+# ---------------------------------------------------------------- FP32 and reduced precision
+
+def test_f32_taylor_green_1000_steps_velocity_error():
+    n = 128
+    om = 1.6
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    ref = O.Lattice(n, n, oms).init(rho, u).run(1000)
+    _, u_ref = ref.macros()
+    gpu = lbm.Lattice(n, n, oms, store=lbm.F32).init(rho, u).step(1000)
+    _, u_g = gpu.macros()
+    assert rel_l2(u_g, u_ref) <= 1e-5
+    gpu.close()
+
+
+# Stated bounds for deviation storage (relative L2 velocity error against the
+# FP64 oracle, Taylor-Green, 1000 steps, N = 128 under diffusive scaling).
+REDUCED_BOUNDS = {lbm.BF16DEV: 8e-2, lbm.F16DEV: 2e-3}
+
+
+@pytest.mark.parametrize("store", [lbm.BF16DEV, lbm.F16DEV], ids=["bf16", "f16"])
+def test_reduced_precision_taylor_green_error_is_bounded(store):
+    n = 128
+    om = 1.6
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    ref = O.Lattice(n, n, oms).init(rho, u).run(1000)
+    _, u_ref = ref.macros()
+    gpu = lbm.Lattice(n, n, oms, store=store).init(rho, u).step(1000)
+    _, u_g = gpu.macros()
+    err = rel_l2(u_g, u_ref)
+    print(f"store {lbm.STORE_NAMES[store]}: relative L2 velocity error {err:.3e}")
+    assert err <= REDUCED_BOUNDS[store]
+    gpu.close()
+
+
+# ---------------------------------------------------------------- diagnostics
+
+def test_macros_strain_stats_at_both_parities():
+    gpu, ref = pair(50, 41, lbm.CASCADED, lbm.F64, "couette", force=(3e-5, 1e-5))
+    gpu.set_f(random_state(ref, 21))
+    for k in range(2):
+        gpu.step(1)
+        ref.run(1)
+        rho_g, u_g = gpu.macros()
+        rho_r, u_r = ref.macros()
+        np.testing.assert_allclose(rho_g, rho_r, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(u_g, u_r, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(gpu.strain(), ref.strain(), rtol=0, atol=1e-13)
+        st = gpu.stats()
+        mom_x = (rho_r * u_r[0]).sum()
+        mom_y = (rho_r * u_r[1]).sum()
+        np.testing.assert_allclose(st, [rho_r.sum(), mom_x, mom_y], rtol=1e-12, atol=1e-12)
+    gpu.close()
+
+
+def test_device_pointer_entry_points_agree_with_host_ones():
+    import torch
+
+    n = 40
+    rho, u = workloads.random_fields(3, n, n, u_amp=0.03)
+    a = lbm.Lattice(n, n, OMEGAS, store=lbm.F32, edges=EDGES["cavity"][0], wall_u=EDGES["cavity"][1])
+    b = lbm.Lattice(n, n, OMEGAS, store=lbm.F32, edges=EDGES["cavity"][0], wall_u=EDGES["cavity"][1],
+                    stream=torch.cuda.current_stream().cuda_stream)
+    a.init(rho, u).step(7)
+    b.init_device(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(7)
+    r_b, u_b = b.macros_device()
+    torch.cuda.synchronize()
+    r_a, u_a = a.macros()
+    np.testing.assert_array_equal(r_b.cpu().numpy(), r_a)
+    np.testing.assert_array_equal(u_b.cpu().numpy(), u_a)
+    f = b.get_f_device()
+    c = lbm.Lattice(n, n, OMEGAS, store=lbm.F32, edges=EDGES["cavity"][0], wall_u=EDGES["cavity"][1])
+    c.set_f_device(f)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(c.get_f(), a.get_f())
+    for x in (a, b, c):
+        x.close()
+
+
+def test_divergence_check_stops_an_unstable_run_cleanly():
+    """SRT at a cell Reynolds number far above its stability limit (Sec. V,
+    Table IV) blows up; the check reports it and the context stays usable."""
+    n = 64
+    gpu = lbm.Lattice(n, n, (1.0, 1.995, 1.995, 1.0, 1.0, 1.0), edges=EDGES["cavity"][0],
+                      wall_u=(0, 0, 0, 0.4), model=lbm.BGK, store=lbm.F32).init()
+    gpu.set_check(50, 1e-3)
+    with pytest.raises(lbm.LBMError) as ei:
+        gpu.step(200000)
+    assert ei.value.code == lbm.LBM_EDIVERGED
+    gpu.close()
+    ok = lbm.Lattice(8, 8, OMEGAS, store=lbm.F64).init().step(3)
+    assert np.isfinite(ok.get_f()).all()
+    ok.close()
+
+
+# ---------------------------------------------------------------- full size (the bench workload)
+
+def _patch_reference(n, u0, om, ix, iy, steps):
+    """Post-step populations of node (ix, iy) of the n x n Taylor-Green lattice,
+    from the oracle on the (2 steps + 1)^2 patch around it (periodic wrap)."""
+    r = steps
+    xs = [(ix + k) % n for k in range(-r, r + 1)]
+    ys = [(iy + k) % n for k in range(-r, r + 1)]
+    rho, u = workloads.taylor_green_init(n, u0)
+    prho = rho[np.ix_(ys, xs)]
+    pu = u[:, ys][:, :, xs]
+    m = 2 * r + 1
+    L = O.Lattice(m, m, (1.0, om, om, 1.0, 1.0, 1.0)).init(prho, pu)
+    L.run(steps)
+    return L.f[:, r, r]
+
+
+def test_full_size_taylor_green_4096_sampled_nodes():
+    """The bench workload (4096^2, FP32 storage, one launch per step) against the
+    oracle on sampled nodes, plus global mass conservation after 100 steps."""
+    import torch
+
+    n, om = 4096, 1.6
+    u0 = workloads.diffusive_u0(n)
+    rho, u = workloads.taylor_green_init(n, u0)
+    gpu = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), store=lbm.F32)
+    gpu.init(rho, u)
+    m0 = gpu.stats()[0]
+    rng = np.random.default_rng(4096)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0)] + [tuple(v) for v in rng.integers(0, n, (60, 2))]
+    for steps in (1, 2):
+        if steps == 2:
+            gpu.step(1)
+        else:
+            gpu.step(1)
+        f = gpu.get_f()
+        for ix, iy in pts:
+            ref = _patch_reference(n, u0, om, ix, iy, steps)
+            dev = f[:, iy, ix] - ref
+            assert np.abs(dev).max() <= 2e-8 * 1.0, (ix, iy, steps)
+    gpu.step(98)
+    m1 = gpu.stats()[0]
+    assert abs(m1 - m0) / m0 <= 1e-9
+    gpu.close()
+    torch.cuda.synchronize()
