@@ -29,13 +29,15 @@ __device__ __forceinline__ void node_force_any(const Args& a, int force, int x, 
     }
 }
 
+// Deviations of node (x, y) at the current time in physical units.
 template <int STORE>
 __device__ __forceinline__ void load_any(const Args& a, bool odd, int x, int y, double d[9]) {
     typename Store<STORE>::R r[9];
     if (odd) load_node<STORE, true, true>(a, x, y, r);
     else load_node<STORE, false, true>(a, x, y, r);
+    constexpr double inv = 1.0 / Store<STORE>::scale;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) d[q] = double(r[q]);
+    for (int q = 0; q < 9; ++q) d[q] = double(r[q]) * inv;
 }
 
 // Equilibria used to start a run.  Cascaded: the populations whose central
@@ -75,7 +77,7 @@ __global__ void init_kernel(const Args a, int model, int force, bool ffield_doub
             feq = wgt<double>(q) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
         }
         const double dev = (feq - wgt<double>(q) * a.rho0) - 0.5 * Sq[q];
-        f[q * a.plane + off] = S::enc(R(dev));
+        f[q * a.plane + off] = S::enc(R(dev * S::scale));
     }
 }
 
@@ -90,7 +92,7 @@ __global__ void set_f_kernel(const Args a, const double* src) {
     T* f = static_cast<T*>(a.f);
 #pragma unroll
     for (int q = 0; q < 9; ++q)
-        f[q * a.plane + (long long)y * a.pitch + x] = S::enc(R(src[q * p + n] - wgt<double>(q) * a.rho0));
+        f[q * a.plane + (long long)y * a.pitch + x] = S::enc(R((src[q * p + n] - wgt<double>(q) * a.rho0) * S::scale));
 }
 
 template <int STORE>

@@ -146,6 +146,8 @@ int lbm_create(int nx, int ny, const double omegas[6], const double force[2], co
     if (nx < 1 || ny < 1) return fail(LBM_EINVAL, "nx and ny must be >= 1 (got %d x %d)", nx, ny);
     if ((long long)nx * ny > 0x7fffffffLL) return fail(LBM_EINVAL, "nx * ny exceeds 2^31 - 1");
     if (ny > 65535) return fail(LBM_EINVAL, "ny = %d exceeds 65535", ny);
+    if ((long long)((nx + 31) / 32 * 32) * ny > 0x7fffffffLL)
+        return fail(LBM_EINVAL, "padded plane (nx rounded up to 32) x ny exceeds 2^31 - 1");
     if (!omegas) return fail(LBM_EINVAL, "omegas is NULL");
     for (int k = 0; k < 6; ++k)
         if (!(omegas[k] > 0.0 && omegas[k] < 2.0))
@@ -183,6 +185,7 @@ int lbm_create(int nx, int ny, const double omegas[6], const double force[2], co
     a.ny = ny;
     a.pitch = (nx + 31) / 32 * 32;
     a.plane = (long long)a.pitch * ny;
+    a.scale = lbm::store_scale(store);
     for (int k = 0; k < 6; ++k) a.om[k] = omegas[k];
     a.F[0] = force ? force[0] : 0.0;
     a.F[1] = force ? force[1] : 0.0;

@@ -44,33 +44,42 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opposit
 
 // ---------------------------------------------------------------- storage
 template <int STORE> struct Store;
+// `scale` multiplies the deviation before it is stored.  The step kernels work
+// directly in stored units: the collision is homogeneous of degree one in
+// (d, rho0, F) at fixed velocity (u = j / rho is scale free), so scaling rho0,
+// F and the wall terms by the same factor (prepare_constants) is exact.
 template <> struct Store<LBM_F64> {
     using T = double; using R = double;
+    static constexpr double scale = 1.0;
     static __device__ __forceinline__ R dec(T v) { return v; }
     static __device__ __forceinline__ T enc(R v) { return v; }
 };
 template <> struct Store<LBM_F32> {
     using T = float; using R = float;
+    static constexpr double scale = 1.0;
     static __device__ __forceinline__ R dec(T v) { return v; }
     static __device__ __forceinline__ T enc(R v) { return v; }
 };
 template <> struct Store<LBM_BF16DEV> {
     using T = __nv_bfloat16; using R = float;
+    static constexpr double scale = 1.0;
     static __device__ __forceinline__ R dec(T v) { return __bfloat162float(v); }
     static __device__ __forceinline__ T enc(R v) { return __float2bfloat16_rn(v); }
 };
 // FP16 keeps 4096 x deviation: deviations of 1.5e-8 .. 16 stay normal numbers.
-constexpr float kF16Scale = 4096.0f;
 template <> struct Store<LBM_F16DEV> {
     using T = __half; using R = float;
-    static __device__ __forceinline__ R dec(T v) { return __half2float(v) * (1.0f / kF16Scale); }
-    static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v * kF16Scale); }
+    static constexpr double scale = 4096.0;
+    static __device__ __forceinline__ R dec(T v) { return __half2float(v); }
+    static __device__ __forceinline__ T enc(R v) { return __float2half_rn(v); }
 };
+
+inline double store_scale(int store) { return store == LBM_F16DEV ? Store<LBM_F16DEV>::scale : 1.0; }
 
 // ---------------------------------------------------------------- launch arguments
 // Plain-old-data, passed by value to every kernel.
 // Index of the per-launch constants in Args::kf / Args::kd.
-enum : int { K_C3 = 0, K_W3 = 6, K_RHO0 = 12, K_FX = 13, K_FY = 14, K_COUNT = 16 };
+enum : int { K_C3 = 0, K_W3 = 6, K_RHO0 = 12, K_FX = 13, K_FY = 14, K_SCALE = 15, K_COUNT = 16 };
 
 struct Args {
     void* f;                  // populations [9][ny][pitch] of the stored type
@@ -82,10 +91,11 @@ struct Args {
     double F[2];              // uniform body force
     const void* ffield;       // per-node force [2][ny][nx] (Real), or null
     double rho0;
-    // The constants the kernels use, converted once on the host into both
+    double scale;             // storage scale of the deviations (Store<>::scale)
+    // The constants the step kernels use, converted once on the host into both
     // arithmetic types (GB300's FP64 rate is far too low for per-thread
     // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 18-23),
-    // omega_3 .. omega_8, rho0, F_x, F_y; and the wall terms in FP32.
+    // omega_3 .. omega_8, and rho0, F_x, F_y and the wall terms in stored units.
     float kf[K_COUNT];
     double kd[K_COUNT];
     float wallxf[4], wallyf[4];
@@ -96,12 +106,15 @@ inline void prepare_constants(Args& a) {
     a.kd[K_C3] = a.om[0] / 12.0;
     for (int k = 1; k < 6; ++k) a.kd[K_C3 + k] = a.om[k] / 4.0;
     for (int k = 0; k < 6; ++k) a.kd[K_W3 + k] = a.om[k];
-    a.kd[K_RHO0] = a.rho0;
-    a.kd[K_FX] = a.F[0];
-    a.kd[K_FY] = a.F[1];
-    a.kd[15] = 0.0;
+    a.kd[K_RHO0] = a.rho0 * a.scale;
+    a.kd[K_FX] = a.F[0] * a.scale;
+    a.kd[K_FY] = a.F[1] * a.scale;
+    a.kd[K_SCALE] = a.scale;
     for (int k = 0; k < K_COUNT; ++k) a.kf[k] = float(a.kd[k]);
-    for (int k = 0; k < 4; ++k) { a.wallxf[k] = float(a.wallx[k]); a.wallyf[k] = float(a.wally[k]); }
+    for (int k = 0; k < 4; ++k) {
+        a.wallxf[k] = float(a.wallx[k] * a.scale);
+        a.wallyf[k] = float(a.wally[k] * a.scale);
+    }
 }
 
 template <typename R> __device__ __forceinline__ const R* kconst(const Args& a);
@@ -136,35 +149,43 @@ __device__ __forceinline__ int incoming_wall(const Args& a, int q, int x, int y)
 template <typename R>
 __device__ __forceinline__ R wall_term(const Args& a, int q, int w) {
     if constexpr (sizeof(R) == 4) return wgt<R>(q) * (R(cx(q)) * a.wallxf[w] + R(cy(q)) * a.wallyf[w]);
-    else return wgt<R>(q) * (R(cx(q)) * a.wallx[w] + R(cy(q)) * a.wally[w]);
+    else return wgt<R>(q) * (R(cx(q)) * a.wallx[w] + R(cy(q)) * a.wally[w]);  // FP64 storage: scale 1
 }
 
 // ---------------------------------------------------------------- AA access
-// Load the nine pre-collision deviations of node (x, y).  ODD selects the
-// parity of the step about to be taken (see the header comment).
+// Offsets inside one population plane are 32-bit (pitch * ny < 2^31 is checked
+// at creation); the plane base f + q * plane is the same for every thread.
+template <typename T>
+__device__ __forceinline__ const T* plane_ptr(const Args& a, const T* f, int q) { return f + q * a.plane; }
+template <typename T>
+__device__ __forceinline__ T* plane_ptr(const Args& a, T* f, int q) { return f + q * a.plane; }
+
+// Load the nine pre-collision deviations of node (x, y), in stored units.
+// ODD selects the parity of the step about to be taken (see the header comment).
 template <int STORE, bool ODD, bool WALLS>
 __device__ __forceinline__ void load_node(const Args& a, int x, int y, typename Store<STORE>::R d[9]) {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     const T* __restrict__ f = static_cast<const T*>(a.f);
-    const long long n = (long long)y * a.pitch + x;
+    const int n = y * a.pitch + x;
     if (!ODD) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) d[q] = S::dec(f[q * a.plane + n]);
+        for (int q = 0; q < 9; ++q) d[q] = S::dec(plane_ptr(a, f, q)[n]);
     } else {
         const int xm = x > 0 ? x - 1 : a.nx - 1, xp = x < a.nx - 1 ? x + 1 : 0;
-        const int ym = y > 0 ? y - 1 : a.ny - 1, yp = y < a.ny - 1 ? y + 1 : 0;
+        const int rm = (y > 0 ? y - 1 : a.ny - 1) * a.pitch, rp = (y < a.ny - 1 ? y + 1 : 0) * a.pitch;
+        const int r0 = y * a.pitch;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             int w = -1;
             if (WALLS) w = incoming_wall(a, q, x, y);
             if (w >= 0) {
-                d[q] = S::dec(f[q * a.plane + n]) + wall_term<R>(a, q, w);
+                d[q] = S::dec(plane_ptr(a, f, q)[n]) + wall_term<R>(a, q, w);
             } else {
                 const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
-                const int sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y);
-                d[q] = S::dec(f[opp(q) * a.plane + (long long)sy * a.pitch + sx]);
+                const int sr = cy(q) == 1 ? rm : (cy(q) == -1 ? rp : r0);
+                d[q] = S::dec(plane_ptr(a, f, opp(q))[sr + sx]);
             }
         }
     }
@@ -177,23 +198,24 @@ __device__ __forceinline__ void store_node(const Args& a, int x, int y, const ty
     using T = typename S::T;
     using R = typename S::R;
     T* __restrict__ f = static_cast<T*>(a.f);
-    const long long n = (long long)y * a.pitch + x;
+    const int n = y * a.pitch + x;
     if (!ODD) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) f[opp(q) * a.plane + n] = S::enc(d[q]);
+        for (int q = 0; q < 9; ++q) plane_ptr(a, f, opp(q))[n] = S::enc(d[q]);
     } else {
         const int xm = x > 0 ? x - 1 : a.nx - 1, xp = x < a.nx - 1 ? x + 1 : 0;
-        const int ym = y > 0 ? y - 1 : a.ny - 1, yp = y < a.ny - 1 ? y + 1 : 0;
+        const int rm = (y > 0 ? y - 1 : a.ny - 1) * a.pitch, rp = (y < a.ny - 1 ? y + 1 : 0) * a.pitch;
+        const int r0 = y * a.pitch;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             int w = -1;
             if (WALLS) w = incoming_wall(a, opp(q), x, y);
             if (w >= 0) {
-                f[opp(q) * a.plane + n] = S::enc(d[q] + wall_term<R>(a, opp(q), w));
+                plane_ptr(a, f, opp(q))[n] = S::enc(d[q] + wall_term<R>(a, opp(q), w));
             } else {
                 const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);
-                const int ty = cy(q) == 1 ? yp : (cy(q) == -1 ? ym : y);
-                f[q * a.plane + (long long)ty * a.pitch + tx] = S::enc(d[q]);
+                const int tr = cy(q) == 1 ? rp : (cy(q) == -1 ? rm : r0);
+                plane_ptr(a, f, q)[tr + tx] = S::enc(d[q]);
             }
         }
     }
@@ -203,12 +225,13 @@ __device__ __forceinline__ void store_node(const Args& a, int x, int y, const ty
 template <typename R, int FORCE>
 __device__ __forceinline__ void node_force(const Args& a, int x, int y, R& Fx, R& Fy) {
     if (FORCE == 0) { Fx = R(0); Fy = R(0); return; }
-    Fx = kconst<R>(a)[K_FX]; Fy = kconst<R>(a)[K_FY];
-    if (FORCE == 2) {
+    const R* k = kconst<R>(a);
+    Fx = k[K_FX]; Fy = k[K_FY];
+    if (FORCE == 2) {  // the field is kept in physical units
         const R* ff = static_cast<const R*>(a.ffield);
-        const long long n = (long long)y * a.nx + x;
-        Fx += ff[n];
-        Fy += ff[(long long)a.nx * a.ny + n];
+        const int n = y * a.nx + x;
+        Fx += k[K_SCALE] * ff[n];
+        Fy += k[K_SCALE] * ff[a.nx * a.ny + n];
     }
 }
 
@@ -218,6 +241,15 @@ struct Moments {
     R drho, rho, jx, jy;           // sum d, rho0 + drho, sum d e (momentum of f_bar)
     R kxx, kyy, kxy, kxxy, kxyy, kxxyy;  // raw moments of d (Eq. 16 without the rho0 w part)
 };
+
+// 1/rho: IEEE division in FP64; in FP32 the hardware reciprocal (rcp.approx,
+// relative error below 2^-22), far below the FP32 storage rounding of d.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 template <typename R>
 __device__ __forceinline__ Moments<R> moments(const R d[9], R rho0) {
@@ -283,7 +315,7 @@ __device__ __forceinline__ void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7,
 template <typename R, bool FORCED>
 __device__ __forceinline__ void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
-    const R inv = R(1) / m.rho;
+    const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (28)
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
     const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
@@ -325,7 +357,7 @@ __device__ __forceinline__ void collide_cascaded(R d[9], R Fx, R Fy, const Coef<
 template <typename R, bool FORCED>
 __device__ __forceinline__ void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
-    const R inv = R(1) / m.rho;
+    const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
     const R usq = R(1.5) * (ux * ux + uy * uy);
@@ -347,7 +379,7 @@ __device__ __forceinline__ void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c
 template <typename R, bool FORCED>
 __device__ __forceinline__ void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
-    const R inv = R(1) / m.rho;
+    const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
     const R uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
