@@ -162,6 +162,46 @@ int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state);
  * 9 stores of the stored type (144, 72, 36, 36); 0 for an unknown kind. */
 size_t lbm_bytes_per_update(int store);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant of lbm_stats.  The paper has no counterpart: this is
+ * an interface for callers that cannot call cudaMalloc (code running inside
+ * another framework's memory pool or a fixed device-memory budget, drivers
+ * that forbid allocation after start-up) and so cannot create a handle.
+ *
+ * The caller describes a population array it owns (the layout lbm_create
+ * uses: [9][ny][pitch] deviations f - w rho0 of the stored type, in the
+ * natural layout after an even number of steps, in the AA-swapped layout after
+ * an odd number) and passes a device pointer `out` to 3 doubles, which
+ * receives (sum rho, sum rho u_x, sum rho u_y) exactly as lbm_stats defines
+ * them (uniform force only; no per-node force field).  The call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * runs on the current device.
+ *
+ * Scratch: per-row partial sums live in a file-scope __device__ array of
+ * 3 x LBM_NOALLOC_MAX_ROWS doubles (384 KiB) that every GPU loading this
+ * library holds until the process exits.  ny > LBM_NOALLOC_MAX_ROWS is
+ * rejected with LBM_EINVAL.  The array is shared by all calls and keeps the
+ * last call's values; every call overwrites the rows it reads, so nothing has
+ * to be cleared.  Calls that overlap on the GPU (concurrent streams or host
+ * threads) race on the array and must be serialised by the caller.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Allocates nothing.  Errors: LBM_EINVAL (NULL
+ * pointer, sizes, pitch < nx, unknown store or edge kind), LBM_ECUDA. */
+#define LBM_NOALLOC_MAX_ROWS 16384
+
+typedef struct {
+    int nx, ny;      /* lattice size */
+    int pitch;       /* elements between consecutive rows (>= nx) */
+    int store;       /* LBM_F64, LBM_F32, LBM_BF16DEV or LBM_F16DEV */
+    int odd;         /* nonzero after an odd number of steps */
+    double rho0;     /* reference density of the deviations */
+    double force[2]; /* uniform body force (enters rho u as F/2, Eq. 28) */
+    lbm_bc_t bc;     /* edges and wall speeds, as given to lbm_create */
+} lbm_layout_t;
+
+int lbm_stats_noalloc(const void* f, const lbm_layout_t* layout, double* out, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* lbm_last_error(void);
 

@@ -30,6 +30,9 @@ int stats_blocks(const Args& a);
 cudaError_t launch_stats(const Args& a, int store, bool odd, bool walls, int force, double* partials, double* out,
                          cudaStream_t s);
 
+// Record the message returned by lbm_last_error() and return `code`.
+int set_error(int code, const char* fmt, ...);
+
 // dst[i] = (float)src[i], round to nearest.
 cudaError_t launch_narrow(const double* src, float* dst, size_t n, cudaStream_t s);
 

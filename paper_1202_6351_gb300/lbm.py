@@ -34,6 +34,13 @@ class lbm_bc_t(C.Structure):
     _fields_ = [("edge", C.c_int * 4), ("wall_u", C.c_double * 4)]
 
 
+class lbm_layout_t(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("pitch", C.c_int), ("store", C.c_int), ("odd", C.c_int),
+                ("rho0", C.c_double), ("force", C.c_double * 2), ("bc", lbm_bc_t)]
+
+
+LBM_NOALLOC_MAX_ROWS = 16384
+
 _lib = None
 _vp, _dp, _i, _l, _d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_long, C.c_double
 
@@ -60,6 +67,7 @@ SIGNATURES = {
     "lbm_time": (_l, [_vp]),
     "lbm_info": (_i, [_vp, C.POINTER(C.c_long), C.POINTER(C.c_size_t), C.POINTER(_vp)]),
     "lbm_bytes_per_update": (C.c_size_t, [_i]),
+    "lbm_stats_noalloc": (_i, [_vp, C.POINTER(lbm_layout_t), _vp, _vp]),
     "lbm_last_error": (C.c_char_p, []),
 }
 
