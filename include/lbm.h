@@ -103,6 +103,9 @@ int lbm_set_stream(lbm_t h, void* stream);
 /* Replace the uniform body force (Eq. 5). */
 int lbm_set_force(lbm_t h, const double force[2]);
 
+/* Replace the relaxation rates omega_3..omega_8 (each in (0, 2)). */
+int lbm_set_omegas(lbm_t h, const double omegas[6]);
+
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own
  * copy (FP64 for LBM_F64 storage, FP32 otherwise). */
@@ -161,6 +164,27 @@ int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state);
 /* Algorithmic bytes one lattice update moves for a storage kind: 9 loads and
  * 9 stores of the stored type (144, 72, 36, 36); 0 for an unknown kind. */
 size_t lbm_bytes_per_update(int store);
+
+/* Discrete adjoint of a run (no counterpart in the paper, which has no
+ * gradients): runs `nsteps` steps of the lattice from the transformed
+ * equilibrium at (rho, u0) (as lbm_init_device) with the lattice's current
+ * rates, uniform force and per-node force field, evaluates
+ *     L = 1/2 sum_x |u(x, T) - u_target(x)|^2,   u from Eq. (27)-(28),
+ * and its gradients by the exact discrete adjoint of the FP64/FP32 update:
+ * reverse streaming plus the transposed cascaded collision per node, with the
+ * states recomputed from checkpoints taken every `every` steps.
+ *   rho [ny][nx] (NULL: rho0), u0 and u_target [2][ny][nx]: device, FP64.
+ *   grad_u0, grad_force [2][ny][nx]: device, FP64, may be NULL; grad_force is
+ *   dL/dF at every node (the gradient with respect to the per-node force
+ *   field, whether or not one is set).
+ *   loss (1 double) and grad_omega (dL/d omega_3..omega_8, 6 doubles): host.
+ * Accumulation over time of dL/dF and dL/domega is FP64.  Requirements: the
+ * cascaded model, LBM_F64 or LBM_F32 storage, four periodic edges.  Device
+ * memory used during the call: (ceil(nsteps/every) + min(every, nsteps)) times
+ * the population array, two adjoint arrays and small scratch, allocated and
+ * released in stream order.  Synchronous.  Leaves the lattice at step nsteps. */
+int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const double* u0, const double* u_target,
+                    double* loss, double* grad_u0, double* grad_force, double grad_omega[6]);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free variant of lbm_stats.  The paper has no counterpart: this is

@@ -14,25 +14,6 @@
 
 using lbm::Args;
 
-struct lbm_s {
-    int device = 0;
-    Args a{};
-    int model = 0, store = 0;
-    int edge[4] = {0, 0, 0, 0};
-    double wall_u[4] = {0, 0, 0, 0};
-    bool walls = false;
-    bool has_field = false;
-    long t = 0;
-    cudaStream_t stream = nullptr;
-    void* state = nullptr;
-    size_t state_bytes = 0;
-    void* ffield = nullptr;
-    double* partials = nullptr;  // [3 * stats_blocks] FP64 scratch of lbm_stats
-    double* sums = nullptr;      // [3] device result of lbm_stats
-    long check_every = 0;
-    double check_rtol = 0.0, mass0 = 0.0;
-};
-
 namespace {
 
 thread_local std::string g_error;
@@ -52,6 +33,21 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 }  // namespace
+
+int lbm::force_mode(const lbm_s* h) {
+    if (h->has_field) return 2;
+    return (h->a.F[0] != 0.0 || h->a.F[1] != 0.0) ? 1 : 0;
+}
+
+cudaError_t lbm::launch_step_any(const Args& a, int store, int model, bool odd, int force, bool walls,
+                                 cudaStream_t s) {
+    switch (store) {
+        case LBM_F64: return launch_step_f64(a, model, odd, force, walls, s);
+        case LBM_F32: return launch_step_f32(a, model, odd, force, walls, s);
+        case LBM_BF16DEV: return launch_step_bf16(a, model, odd, force, walls, s);
+        default: return launch_step_f16(a, model, odd, force, walls, s);
+    }
+}
 
 int lbm::set_error(int code, const char* fmt, ...) {
     char buf[512];
@@ -95,19 +91,10 @@ size_t elem_size(int store) {
     }
 }
 
-int force_mode(const lbm_s* h) {
-    if (h->has_field) return 2;
-    return (h->a.F[0] != 0.0 || h->a.F[1] != 0.0) ? 1 : 0;
-}
+using lbm::force_mode;
 
 cudaError_t launch_step(lbm_s* h, bool odd) {
-    const int fm = force_mode(h);
-    switch (h->store) {
-        case LBM_F64: return lbm::launch_step_f64(h->a, h->model, odd, fm, h->walls, h->stream);
-        case LBM_F32: return lbm::launch_step_f32(h->a, h->model, odd, fm, h->walls, h->stream);
-        case LBM_BF16DEV: return lbm::launch_step_bf16(h->a, h->model, odd, fm, h->walls, h->stream);
-        default: return lbm::launch_step_f16(h->a, h->model, odd, fm, h->walls, h->stream);
-    }
+    return lbm::launch_step_any(h->a, h->store, h->model, odd, force_mode(h), h->walls, h->stream);
 }
 
 long long nodes(const lbm_s* h) { return (long long)h->a.nx * h->a.ny; }
@@ -264,6 +251,17 @@ int lbm_set_force(lbm_t h, const double force[2]) {
         return fail(LBM_EINVAL, "force must be two finite numbers");
     h->a.F[0] = force[0];
     h->a.F[1] = force[1];
+    lbm::prepare_constants(h->a);
+    return LBM_OK;
+}
+
+int lbm_set_omegas(lbm_t h, const double omegas[6]) {
+    CHECK_HANDLE(h);
+    if (!omegas) return fail(LBM_EINVAL, "omegas is NULL");
+    for (int k = 0; k < 6; ++k)
+        if (!(omegas[k] > 0.0 && omegas[k] < 2.0))
+            return fail(LBM_EINVAL, "omega_%d = %g is outside (0, 2)", k + 3, omegas[k]);
+    for (int k = 0; k < 6; ++k) h->a.om[k] = omegas[k];
     lbm::prepare_constants(h->a);
     return LBM_OK;
 }

@@ -30,6 +30,8 @@
 
 #include "lbm.h"
 
+#define LBM_HD __host__ __device__ __forceinline__
+
 namespace lbm {
 
 // ---------------------------------------------------------------- lattice
@@ -127,12 +129,14 @@ struct Coef {
     R c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, ..., omega_8/4 (Eq. 18-23)
     R w3, w4, w5, w6, w7, w8;  // the rates themselves (MRT, BGK)
     R rho0;
-    __device__ __forceinline__ explicit Coef(const Args& a) {
-        const R* k = kconst<R>(a);
+    LBM_HD Coef() {}
+    // From a constants array laid out as Args::kf / Args::kd.
+    LBM_HD explicit Coef(const R* k) {
         c3 = k[K_C3]; c4 = k[K_C3 + 1]; c5 = k[K_C3 + 2]; c6 = k[K_C3 + 3]; c7 = k[K_C3 + 4]; c8 = k[K_C3 + 5];
         w3 = k[K_W3]; w4 = k[K_W3 + 1]; w5 = k[K_W3 + 2]; w6 = k[K_W3 + 3]; w7 = k[K_W3 + 4]; w8 = k[K_W3 + 5];
         rho0 = k[K_RHO0];
     }
+    __device__ __forceinline__ explicit Coef(const Args& a) : Coef(kconst<R>(a)) {}
 };
 
 // ---------------------------------------------------------------- walls
@@ -244,15 +248,19 @@ struct Moments {
 
 // 1/rho: IEEE division in FP64; in FP32 the hardware reciprocal (rcp.approx,
 // relative error below 2^-22), far below the FP32 storage rounding of d.
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) {
+LBM_HD double recip(double x) { return 1.0 / x; }
+LBM_HD float recip(float x) {
+#ifdef __CUDA_ARCH__
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+#else
+    return 1.0f / x;
+#endif
 }
 
 template <typename R>
-__device__ __forceinline__ Moments<R> moments(const R d[9], R rho0) {
+LBM_HD Moments<R> moments(const R d[9], R rho0) {
     Moments<R> m;
     const R s13 = d[1] + d[3], s24 = d[2] + d[4];
     const R s56 = d[5] + d[6], s78 = d[7] + d[8];
@@ -272,7 +280,7 @@ __device__ __forceinline__ Moments<R> moments(const R d[9], R rho0) {
 
 // Source S_a (Eq. 14-15) for force (Fx, Fy) at velocity (ux, uy).
 template <typename R>
-__device__ __forceinline__ void source(R ux, R uy, R Fx, R Fy, R S[9]) {
+LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     const R m1 = Fx, m2 = Fy;
     const R m3 = R(6) * (Fx * ux + Fy * uy);
     const R m4 = R(2) * (Fx * ux - Fy * uy);
@@ -294,7 +302,7 @@ __device__ __forceinline__ void source(R ux, R uy, R Fx, R Fy, R S[9]) {
 
 // Add K . g (Eq. 26; g0 = g1 = g2 = 0) to d.
 template <typename R>
-__device__ __forceinline__ void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
+LBM_HD void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
     const R t = R(2) * g3 + g8;
     const R a = g4 - g3;             // f1, f3 share -g3 + g4
     const R b = -g3 - g4;            // f2, f4 share -g3 - g4
@@ -313,7 +321,7 @@ __device__ __forceinline__ void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7,
 // ---------------------------------------------------------------- cascaded collision
 // Sec. II, Eq. (13)-(26), on deviations.  FORCE = 0: no source terms.
 template <typename R, bool FORCED>
-__device__ __forceinline__ void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
+LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (28)
@@ -355,7 +363,7 @@ __device__ __forceinline__ void collide_cascaded(R d[9], R Fx, R Fy, const Coef<
 // ---------------------------------------------------------------- SRT-BGK sibling
 // d~ = d - w (d - d_eq) + (1 - w/2) S with the 2nd-order polynomial f_eq and w = omega_4.
 template <typename R, bool FORCED>
-__device__ __forceinline__ void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
+LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
@@ -377,7 +385,7 @@ __device__ __forceinline__ void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c
 // f~ = f - K D^-1 [L (m - m_eq) - (I - L/2) m_s], L = diag(0,0,0,omega_3..omega_8),
 // basis K of Eq. (3), polynomial equilibrium moments m_eq in closed form.
 template <typename R, bool FORCED>
-__device__ __forceinline__ void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
+LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
@@ -427,7 +435,7 @@ __device__ __forceinline__ void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>
 }
 
 template <int MODEL, typename R, bool FORCED>
-__device__ __forceinline__ void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
+LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
     if (MODEL == LBM_CASCADED) collide_cascaded<R, FORCED>(d, Fx, Fy, c);
     else if (MODEL == LBM_BGK) collide_bgk<R, FORCED>(d, Fx, Fy, c);
     else collide_rawmrt<R, FORCED>(d, Fx, Fy, c);

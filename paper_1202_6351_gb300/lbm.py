@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbm_destroy": (_i, [_vp]),
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_set_force": (_i, [_vp, _dp]),
+    "lbm_set_omegas": (_i, [_vp, _dp]),
     "lbm_set_force_field": (_i, [_vp, _vp, _i]),
     "lbm_init": (_i, [_vp, _vp, _vp]),
     "lbm_init_device": (_i, [_vp, _vp, _vp]),
@@ -67,6 +68,7 @@ SIGNATURES = {
     "lbm_time": (_l, [_vp]),
     "lbm_info": (_i, [_vp, C.POINTER(C.c_long), C.POINTER(C.c_size_t), C.POINTER(_vp)]),
     "lbm_bytes_per_update": (C.c_size_t, [_i]),
+    "lbm_adjoint_run": (_i, [_vp, _l, _l, _vp, _vp, _vp, _dp, _vp, _vp, _dp]),
     "lbm_stats_noalloc": (_i, [_vp, C.POINTER(lbm_layout_t), _vp, _vp]),
     "lbm_last_error": (C.c_char_p, []),
 }
@@ -224,6 +226,9 @@ class Lattice:
     def set_force(self, force):
         lbm_set_force(self.h, force)
 
+    def set_omegas(self, omegas):
+        _check(self.lib.lbm_set_omegas(self.h, _darr(omegas, 6)))
+
     def set_force_field(self, fxy):
         if fxy is None:
             _check(self.lib.lbm_set_force_field(self.h, None, 0))
@@ -307,3 +312,18 @@ class Lattice:
 
     def info(self):
         return lbm_info(self.h)
+
+    def adjoint_run(self, nsteps, every, u0, u_target, rho=None, want_u0=True, want_force=True):
+        """lbm_adjoint_run with float64 CUDA tensors; returns (loss, grad_u0, grad_force, grad_omega[6])."""
+        import torch
+
+        shape2 = (2,) + self.shape
+        gu = torch.empty(shape2, dtype=torch.float64, device="cuda") if want_u0 else None
+        gf = torch.empty(shape2, dtype=torch.float64, device="cuda") if want_force else None
+        loss = C.c_double()
+        gom = (C.c_double * 6)()
+        _check(self.lib.lbm_adjoint_run(
+            self.h, int(nsteps), int(every), _dev(rho, self.shape) if rho is not None else None,
+            _dev(u0, shape2), _dev(u_target, shape2), C.byref(loss),
+            gu.data_ptr() if gu is not None else None, gf.data_ptr() if gf is not None else None, gom))
+        return loss.value, gu, gf, np.array(list(gom))
