@@ -291,6 +291,8 @@ def run_ours(args):
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = run_extras(args, make, timed, lbm, nodes, peak, np)
+        extras["batch"] = run_batch_extras(lbm, torch, np, peak, sp)
+        extras["adjoint"] = run_adjoint_extras(lbm, torch, np, sp)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -356,6 +358,125 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
     out["cost_cascaded_over_rawmrt_f32"] = round(out["rawmrt_f32"]["mlups"] / out["cascaded_f32"]["mlups"] - 1, 4)
     out["cost_note"] = "paper (Sec. V): cascaded about 11.6 % slower than raw MRT, CPU, hardware not stated"
     return out
+
+
+def run_batch_extras(lbm, torch, np, peak, sp):
+    """Batched ensemble: 96 domains (sides log-uniform in [64, 2048], half
+    lid-driven cavities at Re in [100, 5000], half Taylor-Green, FP32 / FP16
+    storage), one persistent launch per step under CUDA graphs of 100 steps,
+    against one lbm_step launch per domain per step; plus the 16384^2 FP16
+    cavity at Re = 5000 as the single-domain roofline point."""
+    from paper_1202_6351_gb300 import workloads
+
+    doms = workloads.batch_domains()
+    Ls, nodes, nbytes = [], 0, 0
+    for i, d in enumerate(doms):
+        n = d["side"]
+        st = lbm.F32 if d["store"] == "f32" else lbm.F16DEV
+        if d["kind"] == "cavity":
+            U = 0.1
+            om = 1.0 / (3.0 * U * (n - 1) / d["re"] + 0.5)
+            L = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), edges=(1, 1, 1, 2), wall_u=(0, 0, 0, U),
+                            store=st, stream=sp)
+            L.init()
+        else:
+            L = lbm.Lattice(n, n, omegas(), store=st, stream=sp)
+            rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+            L.init(rho, u)
+        Ls.append(L)
+        nodes += n * n
+        nbytes += n * n * lbm.lbm_bytes_per_update(st)
+    steps = 200
+    stream = torch.cuda.current_stream()
+    # per-domain launches
+    for L in Ls:
+        L.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for L in Ls:
+            L.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_sep = e0.elapsed_time(e1) / 1e3
+    # one persistent launch per step, graphs of 100 steps, autotuned
+    B = lbm.Batch(Ls)
+    tuned_ms = B.tune(5)
+    info = B.info()
+    bstream = torch.cuda.ExternalStream(info["stream"])
+    B.step(100)
+    B.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(bstream)
+    B.step(steps)
+    f1.record(bstream)
+    B.sync()
+    torch.cuda.synchronize()
+    t_bat = f0.elapsed_time(f1) / 1e3
+    B.close()
+    for L in Ls:
+        L.close()
+    out = {
+        "domains": len(doms), "nodes": nodes, "steps": steps,
+        "per_domain_launches": {"mlups": round(nodes * steps / t_sep / 1e6, 1),
+                                "frac": round(nbytes * steps / t_sep / 1e9 / peak, 4), "launches": steps * len(doms)},
+        "batched": {"mlups": round(nodes * steps / t_bat / 1e6, 1),
+                    "frac": round(nbytes * steps / t_bat / 1e9 / peak, 4), "launches": steps,
+                    "graph_steps": 100, "tuned": {k: v for k, v in info.items() if k != "stream"},
+                    "tuned_ms_per_step": round(tuned_ms, 4)},
+        "speedup_batched_over_per_domain": round(t_sep / t_bat, 3),
+    }
+    # roofline point: one 16384^2 FP16 cavity at Re 5000
+    n = 16384
+    U, re = 0.1, 5000.0
+    om = 1.0 / (3.0 * U * (n - 1) / re + 0.5)
+    L = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), edges=(1, 1, 1, 2), wall_u=(0, 0, 0, U),
+                    store=lbm.F16DEV, stream=sp)
+    L.init()
+    L.step(4)
+    torch.cuda.synchronize()
+    k = 50
+    e0.record(stream)
+    L.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    L.close()
+    out["cavity_16384_f16_re5000"] = {"mlups": round(n * n * k / t / 1e6, 1),
+                                     "frac": round(36 * n * n * k / t / 1e9 / peak, 4), "steps": k,
+                                     "state_gb": round(9 * 2 * n * n / 1e9, 2)}
+    return out
+
+
+def run_adjoint_extras(lbm, torch, np, sp):
+    """The adjoint configuration: periodic 512^2, 16 random divergence-free
+    Fourier modes (amplitude 0.02), 2000 FP32 steps, checkpoints every 100,
+    loss against the analytic Taylor-Green field at t = 2000."""
+    import math
+
+    from paper_1202_6351_gb300 import workloads
+
+    n, steps, every = 512, 2000, 100
+    u0 = torch.from_numpy(workloads.fourier_modes_field(20261202, n, modes=16, amp=0.02, kmax=8)).cuda()
+    nu = (1.0 / OMEGA - 0.5) / 3.0
+    k = 2 * math.pi / n
+    x = torch.arange(n, dtype=torch.float64, device="cuda")
+    Y, X = torch.meshgrid(x, x, indexing="ij")
+    dec = math.exp(-2 * k * k * nu * steps)
+    U0 = 0.04 * 64 / n
+    target = torch.stack([-U0 * torch.cos(k * X) * torch.sin(k * Y) * dec, U0 * torch.sin(k * X) * torch.cos(k * Y) * dec])
+    with lbm.Lattice(n, n, omegas(), store=lbm.F32, stream=sp) as L:
+        L.set_force_field(torch.zeros((2, n, n), dtype=torch.float64, device="cuda"))
+        L.adjoint_run(50, 10, u0, target)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, gu, gf, gom = L.adjoint_run(steps, every, u0, target)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"config": "periodic 512x512, 2000 FP32 steps, checkpoint every 100", "seconds": round(dt, 4),
+            "loss": loss, "d_loss_d_omega_shear": float(gom[1] + gom[2]),
+            "lattice_updates_per_s_incl_forward_recompute_reverse": round(3 * n * n * steps / dt / 1e6, 1)}
 
 
 def run_e2e(args, lbm, torch, np, n, rho_h, u_h, sp, nodes):

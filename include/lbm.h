@@ -187,6 +187,48 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
                     double* loss, double* grad_u0, double* grad_force, double grad_omega[6]);
 
 /* ---------------------------------------------------------------------------
+ * Batches: many independent lattices advanced together (no counterpart in the
+ * paper).  One time step of every lattice in the batch is ONE launch of a
+ * persistent kernel whose CTAs walk a work list of (lattice, tile) items; the
+ * per-node update is exactly that of lbm_step, so results are bitwise equal.
+ * Chunks of `graph_steps` steps (default 100, even) are replayed from a CUDA
+ * graph.  All lattices must share the device and the collision model, use
+ * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage and have no per-node force field;
+ * storage kinds, sizes, edges and uniform forces may differ.  The batch works
+ * on its own stream: lbm_batch_step first waits (on the host) for the
+ * lattices' streams, and later work on those streams waits for the batch.
+ * A lattice must not be stepped on its own while it belongs to a live batch
+ * call; lbm_step between batch calls is fine.  Destroy the batch before its
+ * lattices. */
+typedef struct lbm_batch_s* lbm_batch_t;
+
+/* Errors: LBM_EINVAL (count < 1, NULL or repeated lattice, mixed devices or
+ * models, FP64 storage, a force field), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out);
+int lbm_batch_destroy(lbm_batch_t b);
+
+/* Autotuner: times `trial_steps` launches of every tile shape (128x2, 256x1,
+ * 64x4, 32x8 nodes per 256-thread CTA), work-list order (lattice by lattice,
+ * largest first; or one tile of each lattice in turn) and scheduling policy
+ * (round robin, contiguous chunks, dynamic via an atomic counter) and keeps
+ * the fastest.  The lattices' states are snapshot and restored, so tuning
+ * leaves them unchanged.  best_ms (may be NULL) receives the time per step. */
+int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms);
+
+/* Advance every lattice of the batch by n >= 0 steps (asynchronous). */
+int lbm_batch_step(lbm_batch_t b, long n);
+
+/* Steps per CUDA graph (even, 0..4096; 0 disables graphs). */
+int lbm_batch_set_graph_steps(lbm_batch_t b, int steps);
+
+/* Wait for the batch's queued work. */
+int lbm_batch_sync(lbm_batch_t b);
+
+/* cfg = (tile width, tile height, policy, order, grid CTAs, tiles); stream
+ * receives the batch's cudaStream_t (for timing with events).  Either may be NULL. */
+int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free variant of lbm_stats.  The paper has no counterpart: this is
  * an interface for callers that cannot call cudaMalloc (code running inside
  * another framework's memory pool or a fixed device-memory budget, drivers

@@ -1,0 +1,402 @@
+// lbm_batch.cu -- many independent lattices advanced together: one persistent
+// kernel launch per time step for all of them, CUDA graphs of `graph_steps`
+// launches, and an autotuner that picks the tile shape, the order of the work
+// list and the scheduling policy by timing them on the batch itself.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_batch_impl.cuh"
+
+namespace lbm {
+cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
+int batch_blocks_per_sm_cascaded();
+int batch_blocks_per_sm_bgk();
+int batch_blocks_per_sm_rawmrt();
+}  // namespace lbm
+
+using lbm::BatchDomain;
+
+struct lbm_batch_s {
+    int device = 0;
+    int model = 0;
+    std::vector<lbm_s*> doms;
+    cudaStream_t stream = nullptr;  // internal, non-blocking (graphs are captured on it)
+    cudaEvent_t done = nullptr;
+    BatchDomain* h_doms = nullptr;  // pinned staging of the domain table
+    BatchDomain* d_doms = nullptr;
+    int* d_tiles = nullptr;
+    size_t tiles_cap = 0;  // ints
+    int ntiles = 0;
+    int* d_counters = nullptr;
+    int ncounters = 0;
+    int lbx = 7, policy = lbm::kPolicyRoundRobin, order = 0, grid = 0;
+    int sms = 0;
+    int graph_steps = 100;
+    cudaGraphExec_t graph = nullptr;
+    float tuned_ms = 0.f;
+};
+
+namespace {
+
+constexpr int kShapes[4] = {7, 8, 6, 5};  // log2 of the tile width: 128x2, 256x1, 64x4, 32x8
+
+int fail(int code, const char* msg) { return lbm::set_error(code, "%s", msg); }
+
+long long tiles_of(const lbm_s* h, int lbx) {
+    const int bx = 1 << lbx, by = lbm::kBatchThreads >> lbx;
+    return (long long)((h->a.nx + bx - 1) / bx) * ((h->a.ny + by - 1) / by);
+}
+
+// Work list for tile shape lbx.  order 0: domain after domain, largest domain
+// first; order 1: one tile of each domain in turn (largest first).
+std::vector<int> build_tiles(const lbm_batch_s* b, int lbx, int order) {
+    const int bx = 1 << lbx, by = lbm::kBatchThreads >> lbx;
+    std::vector<int> idx(b->doms.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
+        return (long long)b->doms[p]->a.nx * b->doms[p]->a.ny > (long long)b->doms[q]->a.nx * b->doms[q]->a.ny;
+    });
+    std::vector<int> t;
+    if (order == 0) {
+        for (int d : idx) {
+            const int tx = (b->doms[d]->a.nx + bx - 1) / bx, ty = (b->doms[d]->a.ny + by - 1) / by;
+            for (int j = 0; j < ty; ++j)
+                for (int i = 0; i < tx; ++i) t.insert(t.end(), {d, i, j});
+        }
+    } else {
+        std::vector<long long> next(idx.size(), 0);
+        bool any = true;
+        while (any) {
+            any = false;
+            for (size_t k = 0; k < idx.size(); ++k) {
+                const int d = idx[k];
+                const int tx = (b->doms[d]->a.nx + bx - 1) / bx, ty = (b->doms[d]->a.ny + by - 1) / by;
+                if (next[k] < (long long)tx * ty) {
+                    const long long n = next[k]++;
+                    t.insert(t.end(), {d, int(n % tx), int(n / tx)});
+                    any = true;
+                }
+            }
+        }
+    }
+    return t;
+}
+
+cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int order) {
+    const std::vector<int> t = build_tiles(b, lbx, order);
+    b->ntiles = int(t.size() / 3);
+    return cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+}
+
+// Copies each domain's current arguments and parity into the device table.
+cudaError_t refresh_domains(lbm_batch_s* b) {
+    cudaError_t e = cudaEventSynchronize(b->done);  // the previous upload has finished reading h_doms
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        const lbm_s* h = b->doms[i];
+        BatchDomain& D = b->h_doms[i];
+        D.a = h->a;
+        D.store = h->store;
+        D.walls = h->walls ? 1 : 0;
+        D.force = lbm::force_mode(h);
+        D.parity = int(h->t & 1);
+    }
+    return cudaMemcpyAsync(b->d_doms, b->h_doms, b->doms.size() * sizeof(BatchDomain), cudaMemcpyHostToDevice,
+                           b->stream);
+}
+
+cudaError_t launch(lbm_batch_s* b, int flip, int* counter) {
+    switch (b->model) {
+        case LBM_CASCADED:
+            return lbm::launch_batch_cascaded(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy,
+                                              counter, b->stream);
+        case LBM_BGK:
+            return lbm::launch_batch_bgk(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy, counter,
+                                         b->stream);
+        default:
+            return lbm::launch_batch_rawmrt(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy,
+                                            counter, b->stream);
+    }
+}
+
+// One step outside a graph (the counter of the dynamic policy is reset first).
+cudaError_t launch_single(lbm_batch_s* b, int flip) {
+    if (b->policy == lbm::kPolicyDynamic) {
+        cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch(b, flip, b->d_counters);
+}
+
+void drop_graph(lbm_batch_s* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+cudaError_t build_graph(lbm_batch_s* b) {
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    if (b->policy == lbm::kPolicyDynamic) e = cudaMemsetAsync(b->d_counters, 0, b->graph_steps * sizeof(int), b->stream);
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; ++k) e = launch(b, k & 1, b->d_counters + k);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+int blocks_per_sm(int model) {
+    switch (model) {
+        case LBM_CASCADED: return lbm::batch_blocks_per_sm_cascaded();
+        case LBM_BGK: return lbm::batch_blocks_per_sm_bgk();
+        default: return lbm::batch_blocks_per_sm_rawmrt();
+    }
+}
+
+// Work on the domains' own streams that precedes the batch must finish first.
+cudaError_t wait_for_domains(lbm_batch_s* b) {
+    std::vector<cudaStream_t> seen;
+    for (lbm_s* h : b->doms) {
+        if (std::find(seen.begin(), seen.end(), h->stream) != seen.end()) continue;
+        seen.push_back(h->stream);
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Later work on the domains' streams waits for the batch.
+cudaError_t release_domains(lbm_batch_s* b) {
+    cudaError_t e = cudaEventRecord(b->done, b->stream);
+    std::vector<cudaStream_t> seen;
+    for (lbm_s* h : b->doms) {
+        if (e != cudaSuccess) break;
+        if (std::find(seen.begin(), seen.end(), h->stream) != seen.end()) continue;
+        seen.push_back(h->stream);
+        e = cudaStreamWaitEvent(h->stream, b->done, 0);
+    }
+    return e;
+}
+
+#define BATCH_CUDA(call, what)                                                              \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return lbm::set_error(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, \
+                                  "%s: %s", what, cudaGetErrorString(e_));                  \
+    } while (0)
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
+    if (!lattices || count < 1 || !out) return fail(LBM_EINVAL, "lbm_batch_create: need count >= 1 lattices and out");
+    const lbm_s* first = lattices[0];
+    if (!first) return fail(LBM_EINVAL, "lbm_batch_create: null lattice");
+    for (int i = 0; i < count; ++i) {
+        const lbm_s* h = lattices[i];
+        if (!h) return fail(LBM_EINVAL, "lbm_batch_create: null lattice");
+        if (h->device != first->device) return fail(LBM_EINVAL, "lbm_batch_create: lattices on different devices");
+        if (h->model != first->model) return fail(LBM_EINVAL, "lbm_batch_create: lattices of different models");
+        if (h->store != LBM_F32 && h->store != LBM_F16DEV && h->store != LBM_BF16DEV)
+            return fail(LBM_EINVAL, "lbm_batch_create: storage must be LBM_F32, LBM_BF16DEV or LBM_F16DEV");
+        if (h->has_field) return fail(LBM_EINVAL, "lbm_batch_create: per-node force fields are not batched");
+        for (int j = 0; j < i; ++j)
+            if (lattices[j] == h) return fail(LBM_EINVAL, "lbm_batch_create: a lattice appears twice");
+    }
+    Guard g(first->device);
+    lbm_batch_s* b = new lbm_batch_s;
+    b->device = first->device;
+    b->model = first->model;
+    for (int i = 0; i < count; ++i) b->doms.push_back(lattices[i]);
+    long long maxtiles = 0;
+    for (int lbx : kShapes) {
+        long long n = 0;
+        for (lbm_s* h : b->doms) n += tiles_of(h, lbx);
+        maxtiles = std::max(maxtiles, n);
+    }
+    if (maxtiles > 0x7fffffffLL / 3) {
+        delete b;
+        return fail(LBM_EINVAL, "lbm_batch_create: too many tiles");
+    }
+    b->tiles_cap = size_t(3 * maxtiles);
+    b->ncounters = 1 << 12;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_doms, count * sizeof(BatchDomain));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_doms, count * sizeof(BatchDomain));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, b->tiles_cap * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, b->ncounters * sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) {
+        b->grid = b->sms * blocks_per_sm(b->model);
+        e = upload_tiles(b, b->lbx, b->order);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return lbm::set_error(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "lbm_batch_create: %s",
+                              cudaGetErrorString(e));
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch_t b) {
+    if (!b) return LBM_OK;
+    Guard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_doms) cudaFree(b->d_doms);
+    if (b->h_doms) cudaFreeHost(b->h_doms);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_graph_steps(lbm_batch_t b, int steps) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (steps < 0 || (steps & 1) || steps > b->ncounters)
+        return fail(LBM_EINVAL, "lbm_batch_set_graph_steps: steps must be even, >= 0 and <= 4096");
+    Guard g(b->device);
+    BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_set_graph_steps");
+    drop_graph(b);
+    b->graph_steps = steps;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_t b, long n) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (n < 0) return fail(LBM_EINVAL, "lbm_batch_step: n must be >= 0");
+    if (n == 0) return LBM_OK;
+    Guard g(b->device);
+    BATCH_CUDA(wait_for_domains(b), "lbm_batch_step: waiting for the lattices' streams");
+    BATCH_CUDA(refresh_domains(b), "lbm_batch_step: domain table");
+    long done = 0;
+    if (b->graph_steps > 0 && n >= b->graph_steps) {
+        if (!b->graph) BATCH_CUDA(build_graph(b), "lbm_batch_step: graph capture");
+        for (; n - done >= b->graph_steps; done += b->graph_steps)
+            BATCH_CUDA(cudaGraphLaunch(b->graph, b->stream), "lbm_batch_step: graph launch");
+    }
+    for (long k = done; k < n; ++k) BATCH_CUDA(launch_single(b, int((k - done) & 1)), "lbm_batch_step: launch");
+    for (lbm_s* h : b->doms) h->t += n;
+    BATCH_CUDA(release_domains(b), "lbm_batch_step: event");
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch_t b) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    Guard g(b->device);
+    BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_sync");
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (trial_steps < 1) return fail(LBM_EINVAL, "lbm_batch_tune: trial_steps must be >= 1");
+    Guard g(b->device);
+    BATCH_CUDA(wait_for_domains(b), "lbm_batch_tune: waiting for the lattices' streams");
+    BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_tune");
+    // snapshot every domain (the trial steps must leave the states unchanged)
+    size_t total = 0;
+    for (lbm_s* h : b->doms) total += h->state_bytes;
+    char* backup = nullptr;
+    BATCH_CUDA(cudaMallocAsync((void**)&backup, total, b->stream), "lbm_batch_tune: snapshot allocation");
+    auto copy_all = [&](bool save) {
+        size_t off = 0;
+        cudaError_t e = cudaSuccess;
+        for (lbm_s* h : b->doms) {
+            if (e == cudaSuccess)
+                e = save ? cudaMemcpyAsync(backup + off, h->state, h->state_bytes, cudaMemcpyDeviceToDevice, b->stream)
+                         : cudaMemcpyAsync(h->state, backup + off, h->state_bytes, cudaMemcpyDeviceToDevice, b->stream);
+            off += h->state_bytes;
+        }
+        return e;
+    };
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = copy_all(true);
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e == cudaSuccess) e = refresh_domains(b);
+    float best = 1e30f;
+    int best_lbx = b->lbx, best_policy = b->policy, best_order = b->order;
+    for (int lbx : kShapes) {
+        for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
+            e = upload_tiles(b, lbx, order);
+            for (int policy = 0; policy < 3 && e == cudaSuccess; ++policy) {
+                b->lbx = lbx;
+                b->order = order;
+                b->policy = policy;
+                for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_single(b, k & 1);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+                for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_single(b, k & 1);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    best_lbx = lbx;
+                    best_policy = policy;
+                    best_order = order;
+                }
+                if (e == cudaSuccess) e = copy_all(false);  // back to the snapshot for the next candidate
+            }
+        }
+    }
+    b->lbx = best_lbx;
+    b->policy = best_policy;
+    b->order = best_order;
+    b->tuned_ms = best / trial_steps;
+    if (e == cudaSuccess) e = upload_tiles(b, b->lbx, b->order);
+    if (e == cudaSuccess) e = copy_all(false);
+    cudaFreeAsync(backup, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    drop_graph(b);
+    if (e != cudaSuccess)
+        return lbm::set_error(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "lbm_batch_tune: %s",
+                              cudaGetErrorString(e));
+    if (best_ms) *best_ms = b->tuned_ms;
+    return LBM_OK;
+}
+
+int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (cfg) {
+        cfg[0] = 1 << b->lbx;
+        cfg[1] = lbm::kBatchThreads >> b->lbx;
+        cfg[2] = b->policy;
+        cfg[3] = b->order;
+        cfg[4] = b->grid;
+        cfg[5] = b->ntiles;
+    }
+    if (stream) *stream = b->stream;
+    return LBM_OK;
+}
+
+}  // extern "C"

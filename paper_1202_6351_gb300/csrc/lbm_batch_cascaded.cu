@@ -1,0 +1,15 @@
+// lbm_batch_cascaded.cu -- persistent batch kernel for the cascaded collision.
+#include "lbm_batch_impl.cuh"
+
+namespace lbm {
+cudaError_t launch_batch_cascaded(int grid, const BatchDomain* doms, const int* tiles, int ntiles, int lbx, int flip,
+                            int policy, int* counter, cudaStream_t s) {
+    batch_kernel<LBM_CASCADED><<<grid, kBatchThreads, 0, s>>>(doms, tiles, ntiles, lbx, flip, policy, counter);
+    return cudaGetLastError();
+}
+int batch_blocks_per_sm_cascaded() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<LBM_CASCADED>, kBatchThreads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+}  // namespace lbm

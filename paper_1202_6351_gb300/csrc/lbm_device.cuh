@@ -441,4 +441,18 @@ LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
     else collide_rawmrt<R, FORCED>(d, Fx, Fy, c);
 }
 
+// ---------------------------------------------------------------- one node, one step
+// a1-a9: AA-pattern load, decode, force, collision, encode, AA-pattern store.
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+__device__ __forceinline__ void step_node(const Args& a, int x, int y) {
+    using R = typename Store<STORE>::R;
+    const Coef<R> c(a);
+    R d[9];
+    load_node<STORE, ODD, WALLS>(a, x, y, d);
+    R Fx, Fy;
+    node_force<R, FORCE>(a, x, y, Fx, Fy);
+    collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
+    store_node<STORE, ODD, WALLS>(a, x, y, d);
+}
+
 }  // namespace lbm

@@ -14,17 +14,10 @@ namespace lbm {
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
-    using R = typename Store<STORE>::R;
     const int x = blockIdx.x * kStepBX + threadIdx.x;
     const int y = blockIdx.y * kStepBY + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    const Coef<R> c(a);
-    R d[9];
-    load_node<STORE, ODD, WALLS>(a, x, y, d);
-    R Fx, Fy;
-    node_force<R, FORCE>(a, x, y, Fx, Fy);
-    collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
-    store_node<STORE, ODD, WALLS>(a, x, y, d);
+    step_node<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
 }
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>

@@ -69,6 +69,13 @@ SIGNATURES = {
     "lbm_info": (_i, [_vp, C.POINTER(C.c_long), C.POINTER(C.c_size_t), C.POINTER(_vp)]),
     "lbm_bytes_per_update": (C.c_size_t, [_i]),
     "lbm_adjoint_run": (_i, [_vp, _l, _l, _vp, _vp, _vp, _dp, _vp, _vp, _dp]),
+    "lbm_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_vp)]),
+    "lbm_batch_destroy": (_i, [_vp]),
+    "lbm_batch_tune": (_i, [_vp, _i, C.POINTER(C.c_float)]),
+    "lbm_batch_step": (_i, [_vp, _l]),
+    "lbm_batch_set_graph_steps": (_i, [_vp, _i]),
+    "lbm_batch_sync": (_i, [_vp]),
+    "lbm_batch_info": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "lbm_stats_noalloc": (_i, [_vp, C.POINTER(lbm_layout_t), _vp, _vp]),
     "lbm_last_error": (C.c_char_p, []),
 }
@@ -327,3 +334,58 @@ class Lattice:
             _dev(u0, shape2), _dev(u_target, shape2), C.byref(loss),
             gu.data_ptr() if gu is not None else None, gf.data_ptr() if gf is not None else None, gom))
         return loss.value, gu, gf, np.array(list(gom))
+
+
+class Batch:
+    """Many lattices advanced by one persistent launch per step (lbm_batch_*)."""
+
+    POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic"}
+    ORDERS = {0: "largest_first", 1: "interleaved"}
+
+    def __init__(self, lattices):
+        self.lib = load_library()
+        self.lattices = list(lattices)  # keep the handles alive
+        arr = (C.c_void_p * len(self.lattices))(*[L.h.value if isinstance(L.h, C.c_void_p) else L.h
+                                                   for L in self.lattices])
+        self.b = C.c_void_p()
+        _check(self.lib.lbm_batch_create(arr, len(self.lattices), C.byref(self.b)))
+
+    def close(self):
+        if self.b is not None:
+            _check(self.lib.lbm_batch_destroy(self.b))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def tune(self, trial_steps=5):
+        ms = C.c_float()
+        _check(self.lib.lbm_batch_tune(self.b, int(trial_steps), C.byref(ms)))
+        return ms.value
+
+    def step(self, n=1):
+        _check(self.lib.lbm_batch_step(self.b, int(n)))
+        return self
+
+    def set_graph_steps(self, steps):
+        _check(self.lib.lbm_batch_set_graph_steps(self.b, int(steps)))
+
+    def sync(self):
+        _check(self.lib.lbm_batch_sync(self.b))
+
+    def info(self):
+        cfg = (C.c_int * 6)()
+        st = C.c_void_p()
+        _check(self.lib.lbm_batch_info(self.b, cfg, C.byref(st)))
+        return {"tile": (cfg[0], cfg[1]), "policy": self.POLICIES[cfg[2]], "order": self.ORDERS[cfg[3]],
+                "grid": cfg[4], "tiles": cfg[5], "stream": st.value or 0}

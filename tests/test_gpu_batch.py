@@ -1,0 +1,109 @@
+"""Batched persistent launch (lbm_batch_*, through the C ABI).
+
+The batch runs the same per-node update as lbm_step, so every lattice of a
+batch must end bit-for-bit where the same lattice stepped alone ends; that
+single-lattice path is itself pinned to the oracle (test_gpu_parity).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1202_6351_gb300 import lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+P, BB, MW = lbm.PERIODIC, lbm.BOUNCEBACK, lbm.MOVING_WALL
+OM = (1.1, 1.7, 1.7, 1.0, 1.2, 0.9)
+
+# (nx, ny, store, edges, wall_u, force, init)
+DOMAINS = [
+    (64, 64, lbm.F32, (P, P, P, P), (0, 0, 0, 0), (0, 0), "tg"),
+    (50, 37, lbm.F16DEV, (BB, BB, BB, MW), (0, 0, 0, 0.1), (0, 0), "rest"),
+    (33, 20, lbm.BF16DEV, (P, P, BB, BB), (0, 0, 0, 0), (2e-5, 0), "rest"),
+    (100, 100, lbm.F16DEV, (P, P, P, P), (0, 0, 0, 0), (0, 0), "tg"),
+    (129, 97, lbm.F32, (BB, BB, BB, MW), (0, 0, 0, 0.08), (0, 0), "random"),
+    (5, 3, lbm.F32, (P, P, P, P), (0, 0, 0, 0), (1e-4, -1e-4), "random"),
+    (1, 1, lbm.F32, (P, P, P, P), (0, 0, 0, 0), (0, 0), "random"),
+    (260, 7, lbm.F16DEV, (MW, MW, P, P), (0.02, -0.03, 0, 0), (0, 1e-5), "random"),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+
+
+def make(spec, seed):
+    nx, ny, store, edges, wall_u, force, init = spec
+    L = lbm.Lattice(nx, ny, OM, force=force, edges=edges, wall_u=wall_u, store=store)
+    if init == "tg":
+        rho, u = workloads.taylor_green_init(nx, 0.03)
+        L.init(rho, u)
+    elif init == "random":
+        rho, u = workloads.random_fields(seed, nx, ny, u_amp=0.03, rho_amp=0.01)
+        L.init(rho, u)
+    else:
+        L.init()
+    return L
+
+
+@pytest.mark.parametrize("tune", [False, True], ids=["default", "tuned"])
+def test_batch_is_bitwise_equal_to_single_lattice_steps(tune):
+    alone = [make(s, i) for i, s in enumerate(DOMAINS)]
+    batched = [make(s, i) for i, s in enumerate(DOMAINS)]
+    # start two lattices one step ahead: the batch handles mixed parities
+    for k in (1, 4):
+        alone[k].step(1)
+        batched[k].step(1)
+    with lbm.Batch(batched) as B:
+        B.set_graph_steps(10)
+        if tune:
+            before = [L.get_f() for L in batched]
+            B.tune(3)
+            for L, f in zip(batched, before):
+                np.testing.assert_array_equal(L.get_f(), f)  # tuning leaves the states unchanged
+        B.step(37)  # three graphs of 10 steps and 7 single launches
+        B.step(3)
+        B.sync()
+    for L in alone:
+        L.step(40)
+    for i, (a, b) in enumerate(zip(alone, batched)):
+        assert a.time == b.time
+        np.testing.assert_array_equal(a.get_f(), b.get_f(), err_msg=f"domain {i}")
+    for L in alone + batched:
+        L.close()
+
+
+def test_batch_cavity_matches_oracle():
+    n, U, re = 65, 0.1, 400.0
+    om = O.omega_from_nu(U * (n - 1) / re)
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    edges = (BB, BB, BB, MW)
+    Ls = [lbm.Lattice(n, n, oms, edges=edges, wall_u=(0, 0, 0, U), store=lbm.F32).init(),
+          lbm.Lattice(40, 40, oms, store=lbm.F16DEV).init()]
+    with lbm.Batch(Ls) as B:
+        B.tune(2)
+        B.step(1000)
+        B.sync()
+    _, u = Ls[0].macros()
+    ref = O.Lattice(n, n, oms, edges=edges, wall_u=(0, 0, 0, U)).init().run(1000)
+    _, u_ref = ref.macros()
+    assert np.sqrt(((u - u_ref) ** 2).sum() / (u_ref ** 2).sum()) <= 1e-5
+    for L in Ls:
+        L.close()
+
+
+def test_batch_rejects_unsupported_lattices():
+    a = lbm.Lattice(8, 8, OM, store=lbm.F64)
+    b = lbm.Lattice(8, 8, OM, store=lbm.F32)
+    c = lbm.Lattice(8, 8, OM, store=lbm.F32, model=lbm.BGK)
+    for group in ([a], [b, c], [b, b]):
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.Batch(group)
+        assert ei.value.code == lbm.LBM_EINVAL
+    for L in (a, b, c):
+        L.close()
