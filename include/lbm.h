@@ -2,10 +2,10 @@
  * lbm.h -- C ABI of the GB300 (sm_103a) cascaded lattice Boltzmann library.
  *
  * The library advances a two-dimensional D2Q9 lattice with the cascaded
- * (central-moment MRT) collision of Ning & Premnath, Sec. II, Eq. (13)-(28),
+ * (central-moment MRT) collision of Ning & Premnath, Sec. II, Eq. (13)-(27),
  * or with one of the two sibling collisions the paper compares it with
  * (SRT-BGK and raw-moment MRT, Sec. IV-V).  One call to lbm_step performs
- * collide-and-stream (Eq. 24-25) at every node in one fused CUDA kernel.
+ * collide-and-stream (Eq. 23-24) at every node in one fused CUDA kernel.
  *
  * Conventions shared by every entry point
  *   - Every function returns an int status: LBM_OK (0) or one of the LBM_E*
@@ -52,7 +52,7 @@ extern "C" {
 #define LBM_NORTH 3
 
 /* collision models */
-#define LBM_CASCADED 0 /* central-moment cascaded collision, Sec. II Eq. (13)-(26) */
+#define LBM_CASCADED 0 /* central-moment cascaded collision, Sec. II Eq. (13)-(25) */
 #define LBM_BGK 1      /* single relaxation time, rate omega_4 (named in Sec. I, V) */
 #define LBM_RAWMRT 2   /* raw-moment MRT in the basis K of Eq. (3) (named in Sec. IV-V) */
 
@@ -76,7 +76,7 @@ typedef struct lbm_s* lbm_t;
 
 /* Create a lattice of nx x ny nodes on the current CUDA device.
  *   omegas  : relaxation rates omega_3..omega_8, each in (0, 2) (Sec. II,
- *             after Eq. 23); omega_4 = omega_5 set the shear viscosity
+ *             after Eq. 22); omega_4 = omega_5 set the shear viscosity
  *             nu = (1/omega_4 - 1/2)/3.  BGK uses omega_4 only.
  *   force   : uniform body force (F_x, F_y) of Eq. (5); NULL means zero.
  *   bc      : edges; NULL means periodic on all four edges.
@@ -113,27 +113,27 @@ int lbm_set_force_field(lbm_t h, const double* fxy, int on_device);
 
 /* Set the populations to the equilibrium of the lattice's model at the given
  * density and velocity, in the transformed variable of Eq. (6):
- * f_bar = f_eq(rho, u) - S(u, F)/2, so that Eq. (27)-(28) return exactly
+ * f_bar = f_eq(rho, u) - S(u, F)/2, so that Eq. (26)-(27) return exactly
  * (rho, u).  The cascaded model uses the equilibrium whose central moments are
- * those of Eq. (11); BGK and raw MRT the second-order polynomial one.
+ * those of Eq. (10); BGK and raw MRT the second-order polynomial one.
  * rho [ny][nx] may be NULL (rho0 everywhere), u [2][ny][nx] may be NULL (rest).
  * Resets the step counter to 0.  _device: device pointers. */
 int lbm_init(lbm_t h, const double* rho, const double* u);
 int lbm_init_device(lbm_t h, const double* rho, const double* u);
 
-/* Advance n >= 0 time steps (collide Eq. 24 + stream Eq. 25 per step), one
+/* Advance n >= 0 time steps (collide Eq. 23 + stream Eq. 24 per step), one
  * fused kernel launch per step, asynchronously on the handle's stream.  With
  * the divergence check on (lbm_set_check) the call synchronises at every
  * check and returns LBM_EDIVERGED when it fails. */
 int lbm_step(lbm_t h, long n);
 
-/* Density [ny][nx] and velocity [2][ny][nx] of Eq. (27)-(28) at the current
+/* Density [ny][nx] and velocity [2][ny][nx] of Eq. (26)-(27) at the current
  * time; either pointer may be NULL.  Host pointers: synchronous. */
 int lbm_macros(lbm_t h, double* rho, double* u);
 int lbm_macros_device(lbm_t h, double* rho, double* u);
 
 /* Local strain-rate quantities from the non-equilibrium moments of
- * f = f_bar + S/2, Eq. (29)-(31) solved exactly for the two normal
+ * f = f_bar + S/2, Eq. (28)-(30) solved exactly for the two normal
  * components: out [3][ny][nx] = (d_x j_x, d_y j_y, d_x j_y + d_y j_x). */
 int lbm_strain(lbm_t h, double* out);
 int lbm_strain_device(lbm_t h, double* out);
@@ -146,7 +146,7 @@ int lbm_get_f_device(lbm_t h, double* f);
 int lbm_set_f_device(lbm_t h, const double* f);
 
 /* Global sums in FP64 over all nodes: out = (sum rho, sum rho u_x, sum rho u_y)
- * with rho u from Eq. (28).  Synchronous; out is host memory. */
+ * with rho u from Eq. (27).  Synchronous; out is host memory. */
 int lbm_stats(lbm_t h, double out[3]);
 
 /* Divergence check: every `every` steps (0 = off) lbm_step computes
@@ -169,7 +169,7 @@ size_t lbm_bytes_per_update(int store);
  * gradients): runs `nsteps` steps of the lattice from the transformed
  * equilibrium at (rho, u0) (as lbm_init_device) with the lattice's current
  * rates, uniform force and per-node force field, evaluates
- *     L = 1/2 sum_x |u(x, T) - u_target(x)|^2,   u from Eq. (27)-(28),
+ *     L = 1/2 sum_x |u(x, T) - u_target(x)|^2,   u from Eq. (26)-(27),
  * and its gradients by the exact discrete adjoint of the FP64/FP32 update:
  * reverse streaming plus the transposed cascaded collision per node, with the
  * states recomputed from checkpoints taken every `every` steps.
@@ -262,7 +262,7 @@ typedef struct {
     int store;       /* LBM_F64, LBM_F32, LBM_BF16DEV or LBM_F16DEV */
     int odd;         /* nonzero after an odd number of steps */
     double rho0;     /* reference density of the deviations */
-    double force[2]; /* uniform body force (enters rho u as F/2, Eq. 28) */
+    double force[2]; /* uniform body force (enters rho u as F/2, Eq. 27) */
     lbm_bc_t bc;     /* edges and wall speeds, as given to lbm_create */
 } lbm_layout_t;
 

@@ -123,7 +123,7 @@ def _kind_of(*xs):
 
 
 def collide_node(model, fb, force=(0.0, 0.0), omegas=(1.0,) * 6):
-    """One node's post-collision populations (cascaded: Eq. 13-26)."""
+    """One node's post-collision populations (cascaded: Eq. 13-25)."""
     kind = _kind_of(fb, force, omegas)
     fb, F, om = _arr(fb, kind, (9,)), _arr(force, kind, (2,)), _arr(omegas, kind, (6,))
     out = np.empty(9, _dtype(kind))
@@ -134,7 +134,7 @@ def collide_node(model, fb, force=(0.0, 0.0), omegas=(1.0,) * 6):
 
 
 def macros_node(fb, force=(0.0, 0.0)):
-    """(rho, ux, uy) of Eq. (27)-(28)."""
+    """(rho, ux, uy) of Eq. (26)-(27)."""
     kind = _kind_of(fb, force)
     fb, F = _arr(fb, kind, (9,)), _arr(force, kind, (2,))
     r = np.empty(3, _dtype(kind))
@@ -143,7 +143,7 @@ def macros_node(fb, force=(0.0, 0.0)):
 
 
 def source_node(u, force):
-    """S_0..S_8 of Eq. (14)-(15)."""
+    """S_0..S_8 of Eq. (14) with the m^s list before it."""
     kind = _kind_of(u, force)
     u, F = _arr(u, kind, (2,)), _arr(force, kind, (2,))
     S = np.empty(9, _dtype(kind))
@@ -162,7 +162,7 @@ def equilibrium_node(model, rho, ux, uy):
 
 
 def strain_node(fb, force=(0.0, 0.0), omegas=(1.0,) * 6):
-    """(d_x j_x, d_y j_y, d_x j_y + d_y j_x) from non-equilibrium moments, Eq. (29)-(31)."""
+    """(d_x j_x, d_y j_y, d_x j_y + d_y j_x) from non-equilibrium moments, Eq. (28)-(30)."""
     kind = _kind_of(fb, force, omegas)
     fb, F, om = _arr(fb, kind, (9,)), _arr(force, kind, (2,)), _arr(omegas, kind, (6,))
     out = np.empty(3, _dtype(kind))
@@ -231,7 +231,7 @@ class Lattice:
         return self
 
     def run(self, nsteps):
-        """nsteps of collide-all (Eq. 24) then stream-all (Eq. 25)."""
+        """nsteps of collide-all (Eq. 23) then stream-all (Eq. 24)."""
         s = self._struct()
         _fn(self.kind, "oracle_run")(C.byref(s), _ptr(self.f), _ptr(self._work), C.c_long(int(nsteps)))
         return self
@@ -250,7 +250,7 @@ class Lattice:
         return self
 
     def macros(self):
-        """(rho[ny,nx], u[2,ny,nx]) of Eq. (27)-(28)."""
+        """(rho[ny,nx], u[2,ny,nx]) of Eq. (26)-(27)."""
         rho = np.empty((self.ny, self.nx), _dtype(self.kind))
         u = np.empty((2, self.ny, self.nx), _dtype(self.kind))
         s = self._struct()
@@ -258,7 +258,7 @@ class Lattice:
         return rho, u
 
     def strain(self):
-        """[3, ny, nx]: d_x j_x, d_y j_y, d_x j_y + d_y j_x (Eq. 29-31)."""
+        """[3, ny, nx]: d_x j_x, d_y j_y, d_x j_y + d_y j_x (Eq. 28-30)."""
         out = np.empty((3, self.ny, self.nx), _dtype(self.kind))
         s = self._struct()
         _fn(self.kind, "oracle_strain")(C.byref(s), _ptr(self.f), _ptr(out))
@@ -279,7 +279,7 @@ def nu_from_omega(omega):
 
 
 def taylor_green(n, u0, nu, t, rho0=1.0, k=None):
-    """Decaying Taylor-Green vortex, Eq. (36)-(41) of Sec. III-B, at integer
+    """Decaying Taylor-Green vortex, Eq. (35)-(40) of Sec. III-B, at integer
     node coordinates x_i = i, y_j = j on an n x n periodic lattice.
     Returns rho[n,n], u[2,n,n], strain S_xx[n,n]."""
     k = 2.0 * math.pi / n if k is None else k
@@ -288,7 +288,7 @@ def taylor_green(n, u0, nu, t, rho0=1.0, k=None):
     dec = math.exp(-2.0 * k * k * nu * t)
     ux = -u0 * np.cos(k * X) * np.sin(k * Y) * dec
     uy = u0 * np.sin(k * X) * np.cos(k * Y) * dec
-    # p = c_s^2 rho; p0 = rho0/3; Eq. (38)/(41): p = p0 - u0^2/4 (cos 2kx + cos 2ky) e^{-4 k^2 nu t}
+    # p = c_s^2 rho; p0 = rho0/3; Eq. (37)/(40): p = p0 - u0^2/4 (cos 2kx + cos 2ky) e^{-4 k^2 nu t}
     p = rho0 / 3.0 - (u0 * u0 / 4.0) * (np.cos(2 * k * X) + np.cos(2 * k * Y)) * dec * dec
     rho = 3.0 * p
     sxx = k * u0 * np.sin(k * X) * np.sin(k * Y) * dec
@@ -312,7 +312,7 @@ def poiseuille_profile(ny, fx, nu):
 
 
 def relative_error_paper(u_c, u_a):
-    """Eq. (35): sum_i ||u_c,i - u_a,i|| / sum_i ||u_a,i|| (Euclidean norm per node)."""
+    """Eq. (34): sum_i ||u_c,i - u_a,i|| / sum_i ||u_a,i|| (Euclidean norm per node)."""
     d = np.sqrt(((np.asarray(u_c) - np.asarray(u_a)) ** 2).sum(axis=0))
     a = np.sqrt((np.asarray(u_a) ** 2).sum(axis=0))
     return float(d.sum() / a.sum())

@@ -6,17 +6,17 @@
  *
  * TEST INFRASTRUCTURE ONLY -- see lbm_oracle.h.  Written for reading, not for
  * speed: every node is handled alone, collision of the whole lattice is done
- * first and streaming second, in the push form in which Eq. (24)-(25) are
+ * first and streaming second, in the push form in which Eq. (23)-(24) are
  * written.  No blocking, fusion or reordering.
  *
  * Readings of the paper that this file takes (each is also listed in the
  * design notes):
  *   - weights w_a (used in Sec. III-C but never printed) are the unique D2Q9
  *     populations whose central moments are (1,0,0,1/3,1/3,0,0,0,1/9) at u = 0,
- *     i.e. Eq. (11) with rho = 1: (4/9, 1/9 x4, 1/36 x4).
- *   - in Eq. (21)-(22) the source moments written without a prime are the raw
+ *     i.e. Eq. (10) with rho = 1: (4/9, 1/9 x4, 1/36 x4).
+ *   - in Eq. (20)-(21) the source moments written without a prime are the raw
  *     moments sigma'_xxy, sigma'_xyy of Eq. (13) (the central ones vanish by
- *     Eq. (10)); only this reading makes the post-collision central moments
+ *     Eq. (11)); only this reading makes the post-collision central moments
  *     equal their relaxation targets.
  *   - the moving-wall correction of Sec. III-C is applied along the wall:
  *     f_b(x) = f~_bbar(x) + 6 w_b rho_w (e_b . U_wall), with rho_w = rho_0.
@@ -24,7 +24,7 @@
  *     i.e. f_bar = f_eq(rho, u) - S/2.
  *   - SRT-BGK and raw-moment MRT are only named by the paper; they are
  *     defined here with the second-order polynomial equilibrium and the same
- *     source S_a of Eq. (15).
+ *     source S_a of Eq. (14).
  */
 #include <string.h>
 #include "lbm_oracle.h"
@@ -52,7 +52,7 @@ static const int KMAT[9][9] = {
 };
 
 /* ------------------------------------------------------------------------ */
-/* Macroscopic fields, Eq. (27)-(28): rho = sum f_bar, rho u = sum f_bar e + F/2 */
+/* Macroscopic fields, Eq. (26)-(27): rho = sum f_bar, rho u = sum f_bar e + F/2 */
 void ONAME(oracle_macros_node)(const real fb[9], const real F[2], real* rho, real* ux, real* uy)
 {
     real r = 0, jx = 0, jy = 0;
@@ -66,12 +66,12 @@ void ONAME(oracle_macros_node)(const real fb[9], const real F[2], real* rho, rea
     *uy = (jy + 0.5 * F[1]) / r;
 }
 
-/* Source term in velocity space: orthogonal source moments m^s of Eq. (14)
- * inverted with K^-1 = D^-1 K^T into S_0..S_8 of Eq. (15). */
+/* Source term in velocity space: orthogonal source moments m^s (the list before Eq. 14)
+ * inverted with K^-1 = D^-1 K^T into S_0..S_8 of Eq. (14). */
 void ONAME(oracle_source)(const real u[2], const real F[2], real S[9])
 {
     const real ux = u[0], uy = u[1], Fx = F[0], Fy = F[1];
-    /* Eq. (14) */
+    /* the m^s list before Eq. (14) */
     const real m1 = Fx;
     const real m2 = Fy;
     const real m3 = 6.0 * (Fx * ux + Fy * uy);
@@ -80,7 +80,7 @@ void ONAME(oracle_source)(const real u[2], const real F[2], real S[9])
     const real m6 = (2.0 - 3.0 * ux * ux) * Fy - 6.0 * Fx * ux * uy;
     const real m7 = (2.0 - 3.0 * uy * uy) * Fx - 6.0 * Fy * uy * ux;
     const real m8 = 6.0 * ((3.0 * uy * uy - 2.0) * Fx * ux + (3.0 * ux * ux - 2.0) * Fy * uy);
-    /* Eq. (15) */
+    /* Eq. (14) */
     S[0] = (1.0 / 9.0) * (-m3 + m8);
     S[1] = (1.0 / 36.0) * (6.0 * m1 - m3 + 9.0 * m4 + 6.0 * m7 - 2.0 * m8);
     S[2] = (1.0 / 36.0) * (6.0 * m2 - m3 - 9.0 * m4 + 6.0 * m6 - 2.0 * m8);
@@ -93,17 +93,17 @@ void ONAME(oracle_source)(const real u[2], const real F[2], real S[9])
 }
 
 /* ------------------------------------------------------------------------ */
-/* Cascaded collision, Sec. II: f~_bar = f_bar + K g^ + S  (Eq. 24, 26). */
+/* Cascaded collision, Sec. II: f~_bar = f_bar + K g^ + S  (Eq. 23, 25). */
 void ONAME(oracle_collide_cascaded)(const real fb[9], const real F[2], const real om[6], real out[9])
 {
     const real w3 = om[0], w4 = om[1], w5 = om[2], w6 = om[3], w7 = om[4], w8 = om[5];
     const real Fx = F[0], Fy = F[1];
 
-    /* Eq. (27)-(28) */
+    /* Eq. (26)-(27) */
     real rho, ux, uy;
     ONAME(oracle_macros_node)(fb, F, &rho, &ux, &uy);
 
-    /* Eq. (16): raw moments of the transformed populations f_bar */
+    /* Eq. (15): raw moments of the transformed populations f_bar */
     const real kxx = fb[1] + fb[3] + fb[5] + fb[6] + fb[7] + fb[8];
     const real kyy = fb[2] + fb[4] + fb[5] + fb[6] + fb[7] + fb[8];
     const real kxy = (fb[5] + fb[7]) - (fb[6] + fb[8]);
@@ -119,7 +119,7 @@ void ONAME(oracle_collide_cascaded)(const real fb[9], const real F[2], const rea
     const real sxyy = Fx * uy * uy + 2.0 * Fy * uy * ux;
     const real sxxyy = 2.0 * Fx * ux * uy * uy + 2.0 * Fy * uy * ux * ux;
 
-    /* Eq. (18)-(23): the collision kernel, in cascade order */
+    /* Eq. (17)-(22): the collision kernel, in cascade order */
     const real g3 = (w3 / 12.0) * ((2.0 / 3.0) * rho + rho * (ux * ux + uy * uy)
                                    - (kxx + kyy) - 0.5 * (sxx + syy));
     const real g4 = (w4 / 4.0) * (rho * (ux * ux - uy * uy) - (kxx - kyy) - 0.5 * (sxx - syy));
@@ -135,12 +135,12 @@ void ONAME(oracle_collide_cascaded)(const real fb[9], const real F[2], const rea
                     - 2.0 * g3 - 0.5 * uy * uy * (3.0 * g3 + g4) - 0.5 * ux * ux * (3.0 * g3 - g4)
                     - 4.0 * ux * uy * g5 - 2.0 * uy * g6 - 2.0 * ux * g7;
 
-    /* Eq. (15) source in velocity space */
+    /* Eq. (14) source in velocity space */
     real S[9];
     const real u[2] = {ux, uy};
     ONAME(oracle_source)(u, F, S);
 
-    /* Eq. (26): explicit post-collision populations (g0 = g1 = g2 = 0) */
+    /* Eq. (25): explicit post-collision populations (g0 = g1 = g2 = 0) */
     out[0] = fb[0] + (-4.0 * (g3 - g8)) + S[0];
     out[1] = fb[1] + (-g3 + g4 + 2.0 * (g7 - g8)) + S[1];
     out[2] = fb[2] + (-g3 - g4 + 2.0 * (g6 - g8)) + S[2];
@@ -191,7 +191,7 @@ static void raw_from_central(const real c[3][3], real ux, real uy, real r[3][3])
 }
 
 /* Cascaded (central-moment) equilibrium of f: the populations whose central
- * moments about u are those of Eq. (11), (rho,0,0,rho/3,rho/3,0,0,0,rho/9). */
+ * moments about u are those of Eq. (10), (rho,0,0,rho/3,rho/3,0,0,0,rho/9). */
 void ONAME(oracle_equilibrium_cascaded)(const real rho_u[3], real out[9])
 {
     const real rho = rho_u[0];
@@ -270,10 +270,10 @@ void ONAME(oracle_collide_rawmrt)(const real fb[9], const real F[2], const real 
     }
 }
 
-/* Local strain rate from non-equilibrium moments, Eq. (29)-(34).  The
+/* Local strain rate from non-equilibrium moments, Eq. (28)-(33).  The
  * moments are those of the untransformed f = f_bar + S/2.  The three relations
- * of Eq. (29)-(31) are solved exactly for the two normal components, which
- * differs from Eq. (32)-(33) as printed only when omega_3 != omega_4.
+ * of Eq. (28)-(30) are solved exactly for the two normal components, which
+ * differs from Eq. (31)-(32) as printed only when omega_3 != omega_4.
  * out = (d_x j_x, d_y j_y, d_x j_y + d_y j_x). */
 void ONAME(oracle_strain_node)(const real fb[9], const real F[2], const real om[6], real out[3])
 {
@@ -289,15 +289,15 @@ void ONAME(oracle_strain_node)(const real fb[9], const real F[2], const real om[
         kyy += EY[a] * EY[a] * f[a];
         kxy += EX[a] * EY[a] * f[a];
     }
-    /* non-equilibrium raw moments f^_3, f^_4, f^_5 (text after Eq. 31) */
+    /* non-equilibrium raw moments f^_3, f^_4, f^_5 (text after Eq. 30) */
     const real n3 = (kxx + kyy) - ((2.0 / 3.0) * rho + rho * (ux * ux + uy * uy));
     const real n4 = (kxx - kyy) - rho * (ux * ux - uy * uy);
     const real n5 = kxy - rho * ux * uy;
-    const real div = -1.5 * om[0] * n3;   /* Eq. (29): d_x j_x + d_y j_y */
-    const real dif = -1.5 * om[1] * n4;   /* Eq. (30): d_x j_x - d_y j_y */
+    const real div = -1.5 * om[0] * n3;   /* Eq. (28): d_x j_x + d_y j_y */
+    const real dif = -1.5 * om[1] * n4;   /* Eq. (29): d_x j_x - d_y j_y */
     out[0] = 0.5 * (div + dif);
     out[1] = 0.5 * (div - dif);
-    out[2] = -3.0 * om[2] * n5;           /* Eq. (31) */
+    out[2] = -3.0 * om[2] * n5;           /* Eq. (30) */
 }
 
 /* ------------------------------------------------------------------------ */
@@ -334,7 +334,7 @@ void ONAME(oracle_init)(const oracle_lattice* L, const real* rho, const real* u,
     }
 }
 
-/* Collision at every node, Eq. (24). */
+/* Collision at every node, Eq. (23). */
 void ONAME(oracle_collide_all)(const oracle_lattice* L, const real* f, real* post)
 {
     const long plane = (long)L->nx * L->ny;
@@ -352,7 +352,7 @@ void ONAME(oracle_collide_all)(const oracle_lattice* L, const real* f, real* pos
     }
 }
 
-/* Streaming, Eq. (25), in push form: f_bar(x + e_a) <- f~_bar_a(x).  A link
+/* Streaming, Eq. (24), in push form: f_bar(x + e_a) <- f~_bar_a(x).  A link
  * leaving the lattice through a periodic edge re-enters on the other side; one
  * leaving through a wall is reflected into the opposite direction at the same
  * node (half-way bounce-back, Sec. III-A), with the moving-wall correction of

@@ -43,7 +43,7 @@ typedef struct {
     int nx, ny;
     int model;            /* ORACLE_CASCADED | ORACLE_BGK | ORACLE_RAWMRT */
     int edge[4];          /* W, E, S, N */
-    real omega[6];        /* omega_3 .. omega_8 (Sec. II, after Eq. 23) */
+    real omega[6];        /* omega_3 .. omega_8 (Sec. II, after Eq. 22) */
     real force[2];        /* uniform body force (F_x, F_y), Eq. 5 */
     real wall_u[4];       /* tangential wall speed per edge (x for S/N, y for W/E) */
     real rho_w;           /* density used in the moving-wall correction */

@@ -3,8 +3,8 @@
 // body force and the relaxation rates).
 //
 // Forward: f^0 = f_eq(rho, u0) - S/2 (Eq. 6, 12), f^{n+1} = P C(f^n; F, omega)
-// (collide Eq. 24, stream Eq. 25), L = 1/2 sum_x |u(x, T) - u_target(x)|^2 with
-// u from Eq. (27)-(28).  Reverse: lambda^T = dL/df^T; for n = T-1 .. 0
+// (collide Eq. 23, stream Eq. 24), L = 1/2 sum_x |u(x, T) - u_target(x)|^2 with
+// u from Eq. (26)-(27).  Reverse: lambda^T = dL/df^T; for n = T-1 .. 0
 //   mu_a(x) = lambda^{n+1}_a(x + e_a)             (transpose of the pull: a push)
 //   lambda^n(x) = (dC/df)^T mu(x)                  (collide_cascaded_vjp, in registers)
 //   dL/dF(x) += (dC/dF)^T mu(x)  (FP64 per node),   dL/dc += (dC/dc)^T mu(x)  (FP64 sums)

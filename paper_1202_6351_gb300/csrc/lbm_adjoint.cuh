@@ -1,6 +1,6 @@
 // lbm_adjoint.cuh -- reverse mode of the cascaded collision (per node, in registers).
 //
-// The forward map is d~ = d + K g(d, F) + S(u, F) (Sec. II, Eq. 13-26, on
+// The forward map is d~ = d + K g(d, F) + S(u, F) (Sec. II, Eq. 13-25, on
 // deviations).  Given mu = dL/dd~ at one node, collide_cascaded_vjp returns
 // dL/dd = (d d~/d d)^T mu, dL/dF (the node's force) and dL/dc (the six
 // coefficients c3 = omega_3/12, c4..c8 = omega_4..8/4).  It recomputes the
@@ -15,7 +15,7 @@
 namespace lbm {
 
 // Adds (dS/du)^T mu and (dS/dF)^T mu to the four accumulators, for the source
-// S = K D^-1 m^s(u, F) of Eq. (14)-(15): dL/dm^s_b = (K^T mu)_b / D_b, with
+// S = K D^-1 m^s(u, F) of Eq. (14) with the m^s list before it: dL/dm^s_b = (K^T mu)_b / D_b, with
 // D = (9, 6, 6, 36, 4, 4, 12, 12, 36), then through the polynomials m^s_b.
 template <typename R>
 LBM_HD void source_vjp(R ux, R uy, R Fx, R Fy, const R mu[9], R& ux_a, R& uy_a, R& Fx_a, R& Fy_a) {
@@ -211,7 +211,7 @@ LBM_HD void collide_cascaded_vjp(const R d[9], R Fx, R Fy, const Coef<R>& c, con
         Fx_a += uy * Pa;  uy_a += Fx * Pa;  Fy_a += ux * Pa;  ux_a += Fy * Pa;
     }
 
-    // source in velocity space, S = K D^-1 m^s (Eq. 14-15)
+    // source in velocity space, S = K D^-1 m^s (Eq. 14 with the m^s list before it)
     source_vjp(ux, uy, Fx, Fy, mu, ux_a, uy_a, Fx_a, Fy_a);
 
     // uxx = ux^2, uyy = uy^2, uxy = ux uy

@@ -41,7 +41,7 @@ __device__ __forceinline__ void load_any(const Args& a, bool odd, int x, int y, 
 }
 
 // Equilibria used to start a run.  Cascaded: the populations whose central
-// moments about u are (rho, 0, 0, rho/3, rho/3, 0, 0, 0, rho/9) (Eq. 11).  Their
+// moments about u are (rho, 0, 0, rho/3, rho/3, 0, 0, 0, rho/9) (Eq. 10).  Their
 // raw moments factor as rho M_m(ux) M_n(uy) with M_0 = 1, M_1 = u, M_2 = 1/3 + u^2,
 // so f_eq(e) = rho phi(e_x; ux) phi(e_y; uy) with phi(0; u) = 2/3 - u^2 and
 // phi(+-1; u) = (1/3 + u^2 +- u)/2.  Siblings: the 2nd-order polynomial.
@@ -106,7 +106,7 @@ __global__ void get_f_kernel(const Args a, bool odd, double* dst) {
     for (int q = 0; q < 9; ++q) dst[q * p + n] = wgt<double>(q) * a.rho0 + d[q];
 }
 
-// rho, rho u (with F/2, Eq. 28) and the velocity of one node, FP64.
+// rho, rho u (with F/2, Eq. 27) and the velocity of one node, FP64.
 struct NodeMacros {
     double rho, mx, my, ux, uy, Fx, Fy;
     Moments<double> m;
@@ -137,7 +137,7 @@ __global__ void macros_kernel(const Args a, bool odd, int force, bool ffd, doubl
     if (u) { u[n] = r.ux; u[p + n] = r.uy; }
 }
 
-// Eq. (29)-(31) with the moments of f = f_bar + S/2: sum e_x^2 S = 2 F_x u_x,
+// Eq. (28)-(30) with the moments of f = f_bar + S/2: sum e_x^2 S = 2 F_x u_x,
 // sum e_y^2 S = 2 F_y u_y, sum e_x e_y S = F_x u_y + F_y u_x (Eq. 13).
 template <int STORE>
 __global__ void strain_kernel(const Args a, bool odd, int force, bool ffd, double* out) {

@@ -28,8 +28,8 @@ struct BatchDomain {
 template <int MODEL, int STORE, bool ODD>
 __device__ __forceinline__ void batch_node_store(const BatchDomain& D, int x, int y) {
     if (D.walls) {
-        if (D.force) step_node<MODEL, STORE, ODD, 1, true>(D.a, x, y);
-        else step_node<MODEL, STORE, ODD, 0, true>(D.a, x, y);
+        if (D.force) step_node_split<MODEL, STORE, ODD, 1, true>(D.a, x, y);
+        else step_node_split<MODEL, STORE, ODD, 0, true>(D.a, x, y);
     } else {
         if (D.force) step_node<MODEL, STORE, ODD, 1, false>(D.a, x, y);
         else step_node<MODEL, STORE, ODD, 0, false>(D.a, x, y);

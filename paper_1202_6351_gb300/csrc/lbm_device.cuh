@@ -96,7 +96,7 @@ struct Args {
     double scale;             // storage scale of the deviations (Store<>::scale)
     // The constants the step kernels use, converted once on the host into both
     // arithmetic types (GB300's FP64 rate is far too low for per-thread
-    // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 18-23),
+    // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 17-22),
     // omega_3 .. omega_8, and rho0, F_x, F_y and the wall terms in stored units.
     float kf[K_COUNT];
     double kd[K_COUNT];
@@ -126,7 +126,7 @@ template <> __device__ __forceinline__ const double* kconst<double>(const Args& 
 // Relaxation constants in the arithmetic type.
 template <typename R>
 struct Coef {
-    R c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, ..., omega_8/4 (Eq. 18-23)
+    R c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, ..., omega_8/4 (Eq. 17-22)
     R w3, w4, w5, w6, w7, w8;  // the rates themselves (MRT, BGK)
     R rho0;
     LBM_HD Coef() {}
@@ -243,7 +243,7 @@ __device__ __forceinline__ void node_force(const Args& a, int x, int y, R& Fx, R
 template <typename R>
 struct Moments {
     R drho, rho, jx, jy;           // sum d, rho0 + drho, sum d e (momentum of f_bar)
-    R kxx, kyy, kxy, kxxy, kxyy, kxxyy;  // raw moments of d (Eq. 16 without the rho0 w part)
+    R kxx, kyy, kxy, kxxy, kxyy, kxxyy;  // raw moments of d (Eq. 15 without the rho0 w part)
 };
 
 // 1/rho: IEEE division in FP64; in FP32 the hardware reciprocal (rcp.approx,
@@ -278,7 +278,7 @@ LBM_HD Moments<R> moments(const R d[9], R rho0) {
     return m;
 }
 
-// Source S_a (Eq. 14-15) for force (Fx, Fy) at velocity (ux, uy).
+// Source S_a (Eq. 14 with the m^s list before it) for force (Fx, Fy) at velocity (ux, uy).
 template <typename R>
 LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     const R m1 = Fx, m2 = Fy;
@@ -300,7 +300,7 @@ LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     S[8] = k * (R(6) * (m1 - m2) + R(2) * m3 - R(9) * m5 + R(3) * (m6 - m7) + m8);
 }
 
-// Add K . g (Eq. 26; g0 = g1 = g2 = 0) to d.
+// Add K . g (Eq. 25; g0 = g1 = g2 = 0) to d.
 template <typename R>
 LBM_HD void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
     const R t = R(2) * g3 + g8;
@@ -319,12 +319,12 @@ LBM_HD void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
 }
 
 // ---------------------------------------------------------------- cascaded collision
-// Sec. II, Eq. (13)-(26), on deviations.  FORCE = 0: no source terms.
+// Sec. II, Eq. (13)-(25), on deviations.  FORCE = 0: no source terms.
 template <typename R, bool FORCED>
 LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
-    const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (28)
+    const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (27)
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
     const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
     const R r3 = c.rho0 * R(1.0 / 3.0);
@@ -336,17 +336,17 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
         sxxyy = R(2) * uxy * (Fx * uy + Fy * ux);
     }
     const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;  // full kappa'_xx, kappa'_yy
-    // Eq. (18)-(20)
+    // Eq. (17)-(19)
     const R g3 = c.c3 * (R(2.0 / 3.0) * m.drho + m.rho * (uxx + uyy) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
     const R g4 = c.c4 * (m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy));
     const R g5 = c.c5 * (m.rho * uxy - m.kxy - R(0.5) * sxy);
     const R A = R(3) * g3 + g4, B = R(3) * g3 - g4;
-    // Eq. (21)-(22)
+    // Eq. (20)-(21)
     const R g6 = c.c6 * (R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy)
                - R(0.5) * uy * A - R(2) * ux * g5;
     const R g7 = c.c7 * (R(2) * m.rho * ux * uyy + m.kxyy - R(2) * uy * m.kxy - ux * kyy_t - R(0.5) * sxyy)
                - R(0.5) * ux * B - R(2) * uy * g5;
-    // Eq. (23)
+    // Eq. (22)
     const R g8 = c.c8 * (R(1.0 / 9.0) * m.drho - m.kxxyy + R(3) * m.rho * uxx * uyy
                          + R(2) * (ux * m.kxyy + uy * m.kxxy) - uxx * kyy_t - uyy * kxx_t
                          - R(4) * uxy * m.kxy - R(0.5) * sxxyy)
@@ -407,7 +407,7 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
     const R e7 = m.rho * ux;
     const R e8 = m.drho - R(3) * m.rho * usq;
     R s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0, s8 = 0;
-    if (FORCED) {  // Eq. (14)
+    if (FORCED) {  // the m^s list before Eq. (14)
         s3 = R(6) * (Fx * ux + Fy * uy); s4 = R(2) * (Fx * ux - Fy * uy); s5 = Fx * uy + Fy * ux;
         s6 = (R(2) - R(3) * uxx) * Fy - R(6) * Fx * ux * uy;
         s7 = (R(2) - R(3) * uyy) * Fx - R(6) * Fy * uy * ux;
@@ -453,6 +453,16 @@ __device__ __forceinline__ void step_node(const Args& a, int x, int y) {
     node_force<R, FORCE>(a, x, y, Fx, Fy);
     collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
     store_node<STORE, ODD, WALLS>(a, x, y, d);
+}
+
+// As step_node; with walls, only nodes on the lattice edge take the wall-aware
+// path (an interior node has no wall link and no wrapped neighbour).
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+__device__ __forceinline__ void step_node_split(const Args& a, int x, int y) {
+    if (WALLS && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)))
+        step_node<MODEL, STORE, ODD, FORCE, true>(a, x, y);
+    else
+        step_node<MODEL, STORE, ODD, FORCE, false>(a, x, y);
 }
 
 }  // namespace lbm

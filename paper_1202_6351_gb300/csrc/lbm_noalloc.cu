@@ -53,7 +53,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;
 }
 
-// One block per row y: sums of rho and rho u (Eq. 27-28, with F/2) over the row.
+// One block per row y: sums of rho and rho u (Eq. 26-27, with F/2) over the row.
 template <int STORE>
 __global__ void __launch_bounds__(kThreads) row_sums_kernel(const Args a, bool odd, double* partials) {
     __shared__ double sh[kThreads / 32];

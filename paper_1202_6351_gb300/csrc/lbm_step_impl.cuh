@@ -2,9 +2,9 @@
 // once per storage type by lbm_step_<store>.cu.
 //
 // One thread per node: AA-pattern load of the nine populations (a1, a2),
-// decode to FP32/FP64 deviations (a3), macroscopic fields (a4, Eq. 27-28),
-// raw moments (a5, Eq. 16), source (a6, Eq. 13-15), cascaded kernel g3..g8
-// (a7, Eq. 18-23) or a sibling collision, back-transform (a8, Eq. 26), encode
+// decode to FP32/FP64 deviations (a3), macroscopic fields (a4, Eq. 26-27),
+// raw moments (a5, Eq. 15), source (a6, Eq. 13-14), cascaded kernel g3..g8
+// (a7, Eq. 17-22) or a sibling collision, back-transform (a8, Eq. 25), encode
 // and AA-pattern store (a9).  All of it in registers, one launch per time step.
 #pragma once
 
@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
     const int x = blockIdx.x * kStepBX + threadIdx.x;
     const int y = blockIdx.y * kStepBY + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    step_node<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
+    step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
 }
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>

@@ -28,8 +28,8 @@ def _table(name):
 E = _table("lattice_vectors.txt")            # [2, 9]: e_ax, e_ay (Eq. 1)
 EX, EY = E[0], E[1]
 K = _table("k_matrix.txt")                   # [9, 9]: Eq. (3)
-KERNEL_MOMENTS = _table("kernel_moments.txt")  # Eq. (17)
-SOURCE_MATRIX = _table("source_matrix.txt")    # 36 * Eq. (15)
+KERNEL_MOMENTS = _table("kernel_moments.txt")  # Eq. (16)
+SOURCE_MATRIX = _table("source_matrix.txt")    # 36 * Eq. (14)
 with open(os.path.join(GOLDEN, "paper_results.json")) as _fh:
     PAPER = json.load(_fh)
 
@@ -78,7 +78,7 @@ def relaxed_central(pre, rho, F, om):
 
 def weights():
     """Populations with central moments (1,0,0,1/3,1/3,0,0,0,1/9) at u = 0,
-    solved from the monomial system (Eq. 11 with rho = 1)."""
+    solved from the monomial system (Eq. 10 with rho = 1)."""
     M = np.array([EX ** m * EY ** n for m, n in ORDERS])
     return np.linalg.solve(M, np.array([1, 0, 0, 1 / 3, 1 / 3, 0, 0, 0, 1 / 9]))
 

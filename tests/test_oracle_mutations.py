@@ -21,7 +21,7 @@ def _relaxation_identity():
 
 
 def _source_moments():
-    T.test_source_central_moments_match_eq10()
+    T.test_source_central_moments_match_eq11()
 
 
 def _streaming():

@@ -46,15 +46,15 @@ def test_columns_of_k_are_orthogonal():
     assert np.abs(KKt - np.diag(np.diag(KKt))).max() > 0
 
 
-def test_collision_kernel_moments_eq17():
+def test_collision_kernel_moments_eq16():
     for row in P.KERNEL_MOMENTS:
         m, n = int(row[0]), int(row[1])
         coeff = [(P.K[:, b] * P.EX ** m * P.EY ** n).sum() for b in range(9)]
         np.testing.assert_array_equal(coeff[3:], row[2:])
 
 
-def test_source_inversion_matrix_eq15_is_d_inverse_k_transpose():
-    # Reading: K^-1 = D^-1 K^T (Eq. 15 printed as K^T D^-1); 36 S_a = sum_b 36 K_ab m_b / D_b
+def test_source_inversion_matrix_eq14_is_d_inverse_k_transpose():
+    # Reading: K^-1 = D^-1 K^T (Eq. 14 printed as K^T D^-1); 36 S_a = sum_b 36 K_ab m_b / D_b
     D = np.diag(P.K.T @ P.K)
     M = 36.0 * P.K / D[None, :]
     np.testing.assert_allclose(M[:, 1:], P.SOURCE_MATRIX[:, 1:], atol=0)
@@ -77,7 +77,7 @@ def test_macros_node_definition():
         assert uy == pytest.approx(((P.EY * fb).sum() + F[1] / 2) / fb.sum(), abs=1e-15)
 
 
-def test_source_central_moments_match_eq10():
+def test_source_central_moments_match_eq11():
     rng = np.random.default_rng(4)
     for _ in range(50):
         u = 0.2 * rng.standard_normal(2)
@@ -85,7 +85,7 @@ def test_source_central_moments_match_eq10():
         S = O.source_node(u, F)
         cm = P.central_moments(S, *u)
         np.testing.assert_allclose(cm, [0, F[0], F[1], 0, 0, 0, 0, 0, 0], atol=2e-16)
-        # Eq. (15) as printed (golden) reproduces S from its orthogonal moments
+        # Eq. (14) as printed (golden) reproduces S from its orthogonal moments
         np.testing.assert_allclose(P.SOURCE_MATRIX @ (P.K.T @ S), 36 * S, atol=1e-15)
 
 
@@ -115,7 +115,7 @@ def test_polynomial_equilibrium_moments():
 @pytest.mark.parametrize("forced", [False, True])
 def test_cascaded_post_collision_central_moments_hit_relaxation_targets(om, forced):
     """The cascaded collision relaxes each central moment (about the pre-collision
-    u) to its target at its own rate (Sec. II, Eq. 18-26)."""
+    u) to its target at its own rate (Sec. II, Eq. 17-25)."""
     rng = np.random.default_rng(7 + int(forced))
     for _ in range(200):
         fb = _random_node(rng)
