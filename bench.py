@@ -349,6 +349,15 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
             "mlups": round(nodes * steps / s / 1e6, 1),
             "frac": round(lbm.lbm_bytes_per_update(st) * nodes * steps / s / 1e9 / peak, 4),
             "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10}
+    # the per-lattice tuner's timings of the two kernel variants on this workload
+    tuned = {}
+    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV)):
+        L = make(lbm.CASCADED, st)
+        ms = L.tune(100)
+        L.close()
+        tuned[name] = {"one_node_per_thread_mlups": round(nodes / ms[0] / 1e3, 1),
+                       "two_rows_packed_fp32x2_mlups": round(nodes / ms[1] / 1e3, 1)}
+    out["kernel_variants"] = tuned
     for name, model in (("bgk", lbm.BGK), ("rawmrt", lbm.RAWMRT)):
         L = make(model, lbm.F32)
         L.step(10)

@@ -106,6 +106,18 @@ int lbm_set_force(lbm_t h, const double force[2]);
 /* Replace the relaxation rates omega_3..omega_8 (each in (0, 2)). */
 int lbm_set_omegas(lbm_t h, const double omegas[6]);
 
+/* Kernel variant of lbm_step for FP32-arithmetic storage (ignored for LBM_F64):
+ * 0 = one node per thread (the default); 1 = two rows per thread with packed
+ * FP32x2 arithmetic.  Both compute the same update; variant 1 may round
+ * differently in the last bit because it fuses multiply-adds explicitly. */
+int lbm_set_variant(lbm_t h, int variant);
+
+/* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
+ * on the lattice itself (the state is snapshot and restored, so it is left
+ * unchanged) and keeps the faster; ms (may be NULL) receives the time per step
+ * of variants 0 and 1 (0 where not run).  Synchronous. */
+int lbm_tune(lbm_t h, int trial_steps, float ms[2]);
+
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own
  * copy (FP64 for LBM_F64 storage, FP32 otherwise). */

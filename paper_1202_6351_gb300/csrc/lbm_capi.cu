@@ -266,6 +266,51 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]) {
     return LBM_OK;
 }
 
+int lbm_set_variant(lbm_t h, int variant) {
+    CHECK_HANDLE(h);
+    if (variant != 0 && variant != 1) return fail(LBM_EINVAL, "variant must be 0 or 1");
+    h->a.variant = h->store == LBM_F64 ? 0 : variant;
+    return LBM_OK;
+}
+
+int lbm_tune(lbm_t h, int trial_steps, float ms[2]) {
+    CHECK_HANDLE(h);
+    if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1");
+    const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
+    if (ms) ms[0] = ms[1] = 0.f;
+    const int nvar = h->store == LBM_F64 ? 1 : 2;
+    void* backup = nullptr;
+    LBM_CUDA(cudaMallocAsync(&backup, h->state_bytes, h->stream), "tune snapshot allocation");
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(backup, h->state, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
+        h->a.variant = v;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+        if (e == cudaSuccess) {
+            if (ms) ms[v] = t / steps;
+            if (t < best) { best = t; best_v = v; }
+            e = cudaMemcpyAsync(h->state, backup, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        }
+    }
+    h->a.variant = best_v;
+    cudaFreeAsync(backup, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_tune");
+    return LBM_OK;
+}
+
 int lbm_set_force_field(lbm_t h, const double* fxy, int on_device) {
     CHECK_HANDLE(h);
     if (!fxy) {

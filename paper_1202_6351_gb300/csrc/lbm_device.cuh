@@ -94,6 +94,7 @@ struct Args {
     const void* ffield;       // per-node force [2][ny][nx] (Real), or null
     double rho0;
     double scale;             // storage scale of the deviations (Store<>::scale)
+    int variant;              // 0: one node per thread; 1: two rows per thread, packed FP32x2 (FP32 arithmetic)
     // The constants the step kernels use, converted once on the host into both
     // arithmetic types (GB300's FP64 rate is far too low for per-thread
     // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 17-22),
@@ -288,7 +289,7 @@ LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     const R m6 = (R(2) - R(3) * ux * ux) * Fy - R(6) * Fx * ux * uy;
     const R m7 = (R(2) - R(3) * uy * uy) * Fx - R(6) * Fy * uy * ux;
     const R m8 = R(6) * ((R(3) * uy * uy - R(2)) * Fx * ux + (R(3) * ux * ux - R(2)) * Fy * uy);
-    const R k = R(1) / R(36);
+    const R k = R(1.0 / 36.0);
     S[0] = k * (R(4) * (m8 - m3));
     S[1] = k * (R(6) * m1 - m3 + R(9) * m4 + R(6) * m7 - R(2) * m8);
     S[2] = k * (R(6) * m2 - m3 - R(9) * m4 + R(6) * m6 - R(2) * m8);

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -20,9 +21,33 @@ __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
     step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
 }
 
+// Two rows per thread (nodes (x, y) and (x, y + 1)) with packed FP32x2
+// arithmetic; a pair that touches a wall edge takes the per-node wall path.
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+__global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const Args a) {
+    const int x = blockIdx.x * kStepBX + threadIdx.x;
+    const int y = 2 * (blockIdx.y * kStepBY + threadIdx.y);
+    if (x >= a.nx || y >= a.ny) return;
+    const bool two = y + 1 < a.ny;
+    if (WALLS && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y + 1 >= a.ny - 1))) {
+        step_node_split<MODEL, STORE, ODD, FORCE, true>(a, x, y);
+        if (two) step_node_split<MODEL, STORE, ODD, FORCE, true>(a, x, y + 1);
+        return;
+    }
+    step_pair<MODEL, STORE, ODD, FORCE>(a, x, y, two);
+}
+
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
     const dim3 block(kStepBX, kStepBY);
+    if constexpr (STORE != LBM_F64) {
+        if (a.variant == 1) {
+            const int rows = (a.ny + 1) / 2;
+            const dim3 grid((a.nx + kStepBX - 1) / kStepBX, (rows + kStepBY - 1) / kStepBY);
+            step_kernel_pair<MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const dim3 grid((a.nx + kStepBX - 1) / kStepBX, (a.ny + kStepBY - 1) / kStepBY);
     step_kernel<MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();

@@ -51,6 +51,8 @@ SIGNATURES = {
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_set_force": (_i, [_vp, _dp]),
     "lbm_set_omegas": (_i, [_vp, _dp]),
+    "lbm_set_variant": (_i, [_vp, _i]),
+    "lbm_tune": (_i, [_vp, _i, C.POINTER(C.c_float)]),
     "lbm_set_force_field": (_i, [_vp, _vp, _i]),
     "lbm_init": (_i, [_vp, _vp, _vp]),
     "lbm_init_device": (_i, [_vp, _vp, _vp]),
@@ -235,6 +237,16 @@ class Lattice:
 
     def set_omegas(self, omegas):
         _check(self.lib.lbm_set_omegas(self.h, _darr(omegas, 6)))
+
+    def set_variant(self, variant):
+        _check(self.lib.lbm_set_variant(self.h, int(variant)))
+        return self
+
+    def tune(self, trial_steps=20):
+        """Time the kernel variants, keep the faster; returns ms per step of variants 0 and 1."""
+        ms = (C.c_float * 2)()
+        _check(self.lib.lbm_tune(self.h, int(trial_steps), ms))
+        return ms[0], ms[1]
 
     def set_force_field(self, fxy):
         if fxy is None:

@@ -304,3 +304,52 @@ def test_full_size_taylor_green_4096_sampled_nodes():
     assert abs(m1 - m0) / m0 <= 1e-9
     gpu.close()
     torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------- packed two-rows-per-thread variant
+
+@pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
+@pytest.mark.parametrize("edges,force", [("periodic", (0.0, 0.0)), ("cavity", (0.0, 0.0)),
+                                         ("channel", (2e-5, 1e-5)), ("allmoving", (0.0, 0.0))])
+def test_pair_variant_matches_oracle_and_scalar_variant(model, edges, force):
+    """Variant 1 (two rows per thread, packed FP32x2) on a 67 x 45 lattice (odd
+    row count: the last thread holds one row) against the oracle and variant 0."""
+    nx, ny, steps = 67, 45, 300
+    e, wu = EDGES[edges]
+    rho, u = workloads.random_fields(8, nx, ny, u_amp=0.03, rho_amp=0.01)
+    ref = O.Lattice(nx, ny, OMEGAS, force=force, edges=e, wall_u=wu, model=model).init(rho, u).run(steps)
+    _, u_ref = ref.macros()
+    out = {}
+    for variant in (0, 1):
+        g = lbm.Lattice(nx, ny, OMEGAS, force=force, edges=e, wall_u=wu, model=model, store=lbm.F32)
+        g.set_variant(variant).init(rho, u).step(steps)
+        out[variant] = g.get_f()
+        _, ug = g.macros()
+        assert rel_l2(ug, u_ref) <= 1e-5, variant
+        g.close()
+    assert rel_max(out[1], out[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("store", [lbm.BF16DEV, lbm.F16DEV], ids=["bf16", "f16"])
+def test_pair_variant_reduced_precision_bound(store):
+    n, om = 128, 1.6
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    ref = O.Lattice(n, n, oms).init(rho, u).run(1000)
+    _, u_ref = ref.macros()
+    g = lbm.Lattice(n, n, oms, store=store).set_variant(1).init(rho, u).step(1000)
+    _, ug = g.macros()
+    assert rel_l2(ug, u_ref) <= REDUCED_BOUNDS[store]
+    g.close()
+
+
+def test_tune_keeps_state_and_picks_a_variant():
+    n = 256
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    g = lbm.Lattice(n, n, OMEGAS, store=lbm.F16DEV).init(rho, u).step(3)
+    before = g.get_f()
+    ms = g.tune(10)
+    assert ms[0] > 0 and ms[1] > 0
+    np.testing.assert_array_equal(g.get_f(), before)
+    assert g.time == 3
+    g.close()
