@@ -42,6 +42,11 @@ def parse():
     p.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
     p.add_argument("--no-extras", action="store_true", help="skip the sibling / precision comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--part", choices=["all", "adjoint", "batch"], default="all",
+                   help="adjoint / batch: run only that measurement and print it (for profiling)")
+    p.add_argument("--adjoint-n", type=int, default=512)
+    p.add_argument("--adjoint-steps", type=int, default=2000)
+    p.add_argument("--batch-steps", type=int, default=200)
     return p.parse_args()
 
 
@@ -49,13 +54,19 @@ def omegas():
     return (1.0, OMEGA, OMEGA, 1.0, 1.0, 1.0)
 
 
+STEP_KERNEL_SOURCES = ("include/lbm.h", "paper_1202_6351_gb300/csrc/lbm_device.cuh",
+                       "paper_1202_6351_gb300/csrc/lbm_internal.h", "paper_1202_6351_gb300/csrc/lbm_pair.cuh",
+                       "paper_1202_6351_gb300/csrc/lbm_step_impl.cuh", "paper_1202_6351_gb300/csrc/lbm_step_f64.cu",
+                       "paper_1202_6351_gb300/csrc/lbm_step_f32.cu", "paper_1202_6351_gb300/csrc/lbm_step_bf16.cu",
+                       "paper_1202_6351_gb300/csrc/lbm_step_f16.cu")
+
+
 def source_digest():
-    """Digest of the CUDA sources, used to tell whether a committed ncu summary
-    still describes the kernel being timed."""
+    """Digest of the sources that define the step kernel, used to tell whether a
+    committed ncu summary still describes the kernel being timed."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1202_6351_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
@@ -292,6 +303,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         extras = run_extras(args, make, timed, lbm, nodes, peak, np)
         extras["batch"] = run_batch_extras(lbm, torch, np, peak, sp)
+        extras["cavity_16384_f16_re5000"] = run_cavity_extras(lbm, torch, peak, sp)
         extras["adjoint"] = run_adjoint_extras(lbm, torch, np, sp)
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -369,7 +381,7 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
     return out
 
 
-def run_batch_extras(lbm, torch, np, peak, sp):
+def run_batch_extras(lbm, torch, np, peak, sp, steps=200):
     """Batched ensemble: 96 domains (sides log-uniform in [64, 2048], half
     lid-driven cavities at Re in [100, 5000], half Taylor-Green, FP32 / FP16
     storage), one persistent launch per step under CUDA graphs of 100 steps,
@@ -395,7 +407,6 @@ def run_batch_extras(lbm, torch, np, peak, sp):
         Ls.append(L)
         nodes += n * n
         nbytes += n * n * lbm.lbm_bytes_per_update(st)
-    steps = 200
     stream = torch.cuda.current_stream()
     # per-domain launches
     for L in Ls:
@@ -436,7 +447,13 @@ def run_batch_extras(lbm, torch, np, peak, sp):
                     "tuned_ms_per_step": round(tuned_ms, 4)},
         "speedup_batched_over_per_domain": round(t_sep / t_bat, 3),
     }
-    # roofline point: one 16384^2 FP16 cavity at Re 5000
+    return out
+
+
+def run_cavity_extras(lbm, torch, peak, sp):
+    """The single-domain roofline point: one 16384^2 FP16-storage cavity at Re 5000."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = 16384
     U, re = 0.1, 5000.0
     om = 1.0 / (3.0 * U * (n - 1) / re + 0.5)
@@ -452,13 +469,11 @@ def run_batch_extras(lbm, torch, np, peak, sp):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     L.close()
-    out["cavity_16384_f16_re5000"] = {"mlups": round(n * n * k / t / 1e6, 1),
-                                     "frac": round(36 * n * n * k / t / 1e9 / peak, 4), "steps": k,
-                                     "state_gb": round(9 * 2 * n * n / 1e9, 2)}
-    return out
+    return {"mlups": round(n * n * k / t / 1e6, 1), "frac": round(36 * n * n * k / t / 1e9 / peak, 4), "steps": k,
+            "state_gb": round(9 * 2 * n * n / 1e9, 2)}
 
 
-def run_adjoint_extras(lbm, torch, np, sp):
+def run_adjoint_extras(lbm, torch, np, sp, n=512, steps=2000):
     """The adjoint configuration: periodic 512^2, 16 random divergence-free
     Fourier modes (amplitude 0.02), 2000 FP32 steps, checkpoints every 100,
     loss against the analytic Taylor-Green field at t = 2000."""
@@ -466,7 +481,7 @@ def run_adjoint_extras(lbm, torch, np, sp):
 
     from paper_1202_6351_gb300 import workloads
 
-    n, steps, every = 512, 2000, 100
+    every = min(100, steps)
     u0 = torch.from_numpy(workloads.fourier_modes_field(20261202, n, modes=16, amp=0.02, kmax=8)).cuda()
     nu = (1.0 / OMEGA - 0.5) / 3.0
     k = 2 * math.pi / n
@@ -483,7 +498,7 @@ def run_adjoint_extras(lbm, torch, np, sp):
         loss, gu, gf, gom = L.adjoint_run(steps, every, u0, target)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-    return {"config": "periodic 512x512, 2000 FP32 steps, checkpoint every 100", "seconds": round(dt, 4),
+    return {"config": f"periodic {n}x{n}, {steps} FP32 steps, checkpoint every {every}", "seconds": round(dt, 4),
             "loss": loss, "d_loss_d_omega_shear": float(gom[1] + gom[2]),
             "lattice_updates_per_s_incl_forward_recompute_reverse": round(3 * n * n * steps / dt / 1e6, 1)}
 
@@ -522,10 +537,30 @@ def run_e2e(args, lbm, torch, np, n, rho_h, u_h, sp, nodes):
             "sequence": "lbm_init(pinned host rho,u) + lbm_step(100) + lbm_macros(pinned host rho,u)"}
 
 
+def run_part(args):
+    """One extra measurement alone (used for profiling captures)."""
+    import numpy as np
+    import torch
+
+    from paper_1202_6351_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    sp = torch.cuda.current_stream().cuda_stream
+    peak, _ = measured_peaks()
+    if args.part == "adjoint":
+        out = run_adjoint_extras(lbm, torch, np, sp, n=args.adjoint_n, steps=args.adjoint_steps)
+    else:
+        out = run_batch_extras(lbm, torch, np, peak, sp, steps=args.batch_steps)
+    print(json.dumps({"part": args.part, **out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.part != "all":
+        return run_part(args)
     return run_ours(args)
 
 

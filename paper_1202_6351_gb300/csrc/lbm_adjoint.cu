@@ -35,16 +35,19 @@ __device__ __forceinline__ void load_rt(const Args& a, bool odd, int x, int y, t
     else load_node<ST, false, false>(a, x, y, d);
 }
 
-// Sums v[0..N) over the block and adds the totals to acc[0..N) (thread 0).
-template <int N>
-__device__ __forceinline__ void block_atomic_add(double (&v)[N], double* acc) {
+// Sums v[0..N) over the block and adds the totals to the FP64 accumulators
+// acc[0..N).  The sum inside a warp runs in the values' own type (FP32 for
+// the FP32 adjoint: a warp adds 32 terms); the warp totals are added in FP64,
+// and so is the accumulation over blocks and time steps.
+template <int N, typename V>
+__device__ __forceinline__ void block_atomic_add(V (&v)[N], double* acc) {
     __shared__ double sh[N][kThreads / 32];
 #pragma unroll
     for (int k = 0; k < N; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int k = 0; k < N; ++k) sh[k][threadIdx.x >> 5] = v[k];
+        for (int k = 0; k < N; ++k) sh[k][threadIdx.x >> 5] = double(v[k]);
     __syncthreads();
     if (threadIdx.x < N) {
         double t = 0.0;
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const Args a, bool o
                                                             double* gc) {
     using R = typename Store<ST>::R;
     const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
-    double c[6] = {0, 0, 0, 0, 0, 0};
+    R c[6] = {0, 0, 0, 0, 0, 0};
     if (x < a.nx) {
         R d[9];
         load_rt<ST>(a, odd, x, y, d);
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const Args a, bool o
         gF[n] += double(g.Fx);
         gF[p + n] += double(g.Fy);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) c[k] = double(g.c[k]);
+        for (int k = 0; k < 6; ++k) c[k] = g.c[k];
     }
     block_atomic_add<6>(c, gc);
 }
