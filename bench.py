@@ -193,6 +193,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dist=None, device="cuda") -> float:
+    """The largest of one float per rank (the timed interval of the slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, seconds: float, world: int) -> float:
+    """Lattice updates of all ranks (weak scaling: each rank its own replica) per second / 1e6."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -283,11 +299,8 @@ def run_ours(args):
     if sampler:
         time.sleep(0.3)
         sampler.stop()
-    secs_t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(secs_t, op=dist.ReduceOp.MAX)
-    secs_max = float(secs_t.item())
-    value = world * nodes * args.steps / secs_max / 1e6
+    secs_max = max_over_ranks(secs, dist, "cuda")
+    value = whole_job_mlups(nodes, args.steps, secs_max, world)
     bpu = lbm.lbm_bytes_per_update(store)
     launch_s = secs / args.steps
     achieved = bpu * nodes / launch_s / 1e9

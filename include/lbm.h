@@ -134,10 +134,17 @@ int lbm_init(lbm_t h, const double* rho, const double* u);
 int lbm_init_device(lbm_t h, const double* rho, const double* u);
 
 /* Advance n >= 0 time steps (collide Eq. 23 + stream Eq. 24 per step), one
- * fused kernel launch per step, asynchronously on the handle's stream.  With
- * the divergence check on (lbm_set_check) the call synchronises at every
+ * fused kernel launch per step, asynchronously on the handle's stream.  Runs
+ * of at least lbm_set_graph_steps steps starting at an even step are replayed
+ * from a CUDA graph on an internal stream that is ordered after the handle's
+ * stream and before any later work on it (the graph is recaptured whenever a
+ * rate, force, force field or variant has changed).  With the divergence
+ * check on (lbm_set_check) no graph is used, the call synchronises at every
  * check and returns LBM_EDIVERGED when it fails. */
 int lbm_step(lbm_t h, long n);
+
+/* Steps per CUDA-graph replay in lbm_step (even; 0 disables graphs; default 64). */
+int lbm_set_graph_steps(lbm_t h, int steps);
 
 /* Density [ny][nx] and velocity [2][ny][nx] of Eq. (26)-(27) at the current
  * time; either pointer may be NULL.  Host pointers: synchronous. */

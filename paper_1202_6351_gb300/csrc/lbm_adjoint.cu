@@ -16,6 +16,7 @@
 #include "lbm.h"
 #include "lbm_adjoint.cuh"
 #include "lbm_internal.h"
+#include "lbm_handle.h"
 
 namespace lbm {
 namespace {

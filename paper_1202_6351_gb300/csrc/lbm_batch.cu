@@ -8,6 +8,7 @@
 
 #include "lbm.h"
 #include "lbm_batch_impl.cuh"
+#include "lbm_handle.h"
 
 namespace lbm {
 cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);

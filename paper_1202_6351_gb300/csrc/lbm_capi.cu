@@ -11,6 +11,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_handle.h"
 
 using lbm::Args;
 
@@ -107,6 +108,62 @@ struct DevBuf {
     cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
     ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
+
+// True if two argument blocks launch the same step kernels on the same data.
+bool same_launch(const Args& x, const Args& y) {
+    if (x.f != y.f || x.plane != y.plane || x.nx != y.nx || x.ny != y.ny || x.pitch != y.pitch) return false;
+    if (x.ffield != y.ffield || x.variant != y.variant || x.scale != y.scale) return false;
+    for (int k = 0; k < 4; ++k)
+        if (x.wall[k] != y.wall[k] || x.wallx[k] != y.wallx[k] || x.wally[k] != y.wally[k] ||
+            x.wallxf[k] != y.wallxf[k] || x.wallyf[k] != y.wallyf[k])
+            return false;
+    for (int k = 0; k < lbm::K_COUNT; ++k)
+        if (x.kd[k] != y.kd[k] || x.kf[k] != y.kf[k]) return false;
+    return true;
+}
+
+void drop_graph(lbm_s* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+// Captures graph_steps launches (even parity first) on the internal stream.
+cudaError_t capture_graph(lbm_s* h, int fm) {
+    drop_graph(h);
+    cudaError_t e = cudaSuccess;
+    if (!h->gstream) e = cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->ev_in) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess && !h->ev_out) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k)
+        e = lbm::launch_step_any(h->a, h->store, h->model, (k & 1) != 0, fm, h->walls, h->gstream);
+    cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) {
+        h->graph_args = h->a;
+        h->graph_force = fm;
+    }
+    return e;
+}
+
+// graph_steps steps from an even step: ordered after prior work on h->stream,
+// and later work on h->stream waits for them.
+cudaError_t replay_graph(lbm_s* h) {
+    const int fm = force_mode(h);
+    cudaError_t e = cudaSuccess;
+    if (!h->graph || fm != h->graph_force || !same_launch(h->a, h->graph_args)) e = capture_graph(h, fm);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gstream, h->ev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->graph, h->gstream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_out, h->gstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_out, 0);
+    return e;
+}
 
 int stats_into(lbm_s* h, double out[3]) {
     LBM_CUDA(lbm::launch_stats(h->a, h->store, h->t & 1, h->walls, force_mode(h), h->partials, h->sums, h->stream),
@@ -229,6 +286,11 @@ int lbm_destroy(lbm_t h) {
         DeviceGuard g(h->device);
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
+        if (h->gstream) cudaStreamSynchronize(h->gstream);
+        drop_graph(h);
+        if (h->ev_in) cudaEventDestroy(h->ev_in);
+        if (h->ev_out) cudaEventDestroy(h->ev_out);
+        if (h->gstream) cudaStreamDestroy(h->gstream);
         if (h->state) cudaFree(h->state);
         if (h->ffield) cudaFree(h->ffield);
         if (h->partials) cudaFree(h->partials);
@@ -263,6 +325,15 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]) {
             return fail(LBM_EINVAL, "omega_%d = %g is outside (0, 2)", k + 3, omegas[k]);
     for (int k = 0; k < 6; ++k) h->a.om[k] = omegas[k];
     lbm::prepare_constants(h->a);
+    return LBM_OK;
+}
+
+int lbm_set_graph_steps(lbm_t h, int steps) {
+    CHECK_HANDLE(h);
+    if (steps < 0 || (steps & 1)) return fail(LBM_EINVAL, "graph steps must be even and >= 0");
+    if (h->gstream) LBM_CUDA(cudaStreamSynchronize(h->gstream), "graph stream sync");
+    drop_graph(h);
+    h->graph_steps = steps;
     return LBM_OK;
 }
 
@@ -375,9 +446,16 @@ int lbm_init(lbm_t h, const double* rho, const double* u) {
 int lbm_step(lbm_t h, long n) {
     CHECK_HANDLE(h);
     if (n < 0) return fail(LBM_EINVAL, "step count must be >= 0");
-    for (long s = 0; s < n; ++s) {
+    for (long s = 0; s < n;) {
+        if (h->graph_steps > 0 && h->check_every == 0 && (h->t & 1) == 0 && n - s >= h->graph_steps) {
+            LBM_CUDA(replay_graph(h), "step graph");
+            h->t += h->graph_steps;
+            s += h->graph_steps;
+            continue;
+        }
         LBM_CUDA(launch_step(h, (h->t & 1) != 0), "step kernel launch");
         ++h->t;
+        ++s;
         if (h->check_every > 0 && h->t % h->check_every == 0) {
             double st[3];
             int rc = stats_into(h, st);

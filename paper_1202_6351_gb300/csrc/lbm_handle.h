@@ -1,0 +1,34 @@
+// lbm_handle.h -- the state behind an lbm_t handle (include/lbm.h), shared by
+// the host-side translation units of the library.
+#pragma once
+
+#include "lbm_internal.h"
+
+// The state behind an lbm_t handle (include/lbm.h).
+struct lbm_s {
+    int device = 0;
+    lbm::Args a{};
+    int model = 0, store = 0;
+    int edge[4] = {0, 0, 0, 0};
+    double wall_u[4] = {0, 0, 0, 0};
+    bool walls = false;
+    bool has_field = false;
+    long t = 0;                  // steps since create / init / set_f (parity selects the AA kernel)
+    cudaStream_t stream = nullptr;
+    void* state = nullptr;       // populations [9][ny][pitch] of the stored type
+    size_t state_bytes = 0;
+    void* ffield = nullptr;      // per-node force [2][ny][nx], FP64 for LBM_F64 storage, FP32 otherwise
+    double* partials = nullptr;  // [3 * stats_blocks] FP64 scratch of lbm_stats
+    double* sums = nullptr;      // [3] device result of lbm_stats
+    long check_every = 0;
+    double check_rtol = 0.0, mass0 = 0.0;
+    // CUDA-graph replay of lbm_step: `graph_steps` launches captured from an even
+    // step on an internal stream, ordered against `stream` by two events; the
+    // launch arguments it was captured with are kept to detect any change.
+    int graph_steps = 64;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    lbm::Args graph_args{};
+    int graph_force = -1;
+};

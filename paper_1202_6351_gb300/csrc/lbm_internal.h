@@ -5,25 +5,7 @@
 
 #include "lbm_device.cuh"
 
-// The state behind an lbm_t handle (include/lbm.h).
-struct lbm_s {
-    int device = 0;
-    lbm::Args a{};
-    int model = 0, store = 0;
-    int edge[4] = {0, 0, 0, 0};
-    double wall_u[4] = {0, 0, 0, 0};
-    bool walls = false;
-    bool has_field = false;
-    long t = 0;                  // steps since create / init / set_f (parity selects the AA kernel)
-    cudaStream_t stream = nullptr;
-    void* state = nullptr;       // populations [9][ny][pitch] of the stored type
-    size_t state_bytes = 0;
-    void* ffield = nullptr;      // per-node force [2][ny][nx], FP64 for LBM_F64 storage, FP32 otherwise
-    double* partials = nullptr;  // [3 * stats_blocks] FP64 scratch of lbm_stats
-    double* sums = nullptr;      // [3] device result of lbm_stats
-    long check_every = 0;
-    double check_rtol = 0.0, mass0 = 0.0;
-};
+struct lbm_s;  // the handle behind lbm_t (lbm_handle.h)
 
 namespace lbm {
 

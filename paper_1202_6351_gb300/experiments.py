@@ -30,9 +30,11 @@ def cavity_omega(n, re, U=0.1):
 
 
 def cavity_steady(n, re, model=lbm.CASCADED, store=lbm.F32, U=0.1, tol=1e-7, check=1000, max_steps=2_000_000,
-                  other_rate=1.0):
+                  other_rate=1.0, fields=False):
     """Run from rest until max |u(t) - u(t - check)| < tol (per `check` steps).
-    Returns (u[2, n, n], steps)."""
+    Returns (u[2, n, n], steps), or with fields=True (rho, u, strain[3, n, n], steps)
+    where strain holds (d_x j_x, d_y j_y, d_x j_y + d_y j_x) from the
+    non-equilibrium moments (Eq. 28-30)."""
     om = cavity_omega(n, re, U)
     rates = (other_rate, om, om, other_rate, other_rate, other_rate)
     with lbm.Lattice(n, n, rates, edges=CAVITY_EDGES, wall_u=(0, 0, 0, U), model=model, store=store) as L:
@@ -43,11 +45,35 @@ def cavity_steady(n, re, model=lbm.CASCADED, store=lbm.F32, U=0.1, tol=1e-7, che
         while steps < max_steps:
             L.step(check)
             steps += check
-            _, u = L.macros()
+            rho, u = L.macros()
             if prev is not None and np.abs(u - prev).max() < tol:
-                return u, steps
+                break
             prev = u
+        if fields:
+            return rho, u, L.strain(), steps
         return u, steps
+
+
+# The five probe points of Sec. IV-C, Table III, in units of the cavity side L.
+TABLE_III_POINTS = {"A": (0.25, 0.5), "B": (0.5, 0.25), "C": (0.5, 0.5), "D": (0.5, 0.75), "E": (0.75, 0.5)}
+
+
+def strain_at_points(rho, u, strain):
+    """dv/dy and du/dy + dv/dx at the Table III points by the two methods of
+    Sec. IV-C: local non-equilibrium moments (strain / rho) and second-order
+    central differences of the velocity.  Node i sits at (i + 1/2)/n; each point
+    takes the nearest node.  Returns {point: (moments_dvdy, fd_dvdy, moments_shear, fd_shear)}."""
+    n = u.shape[1]
+    out = {}
+    for name, (px, py) in TABLE_III_POINTS.items():
+        i = int(round(px * n - 0.5))
+        j = int(round(py * n - 0.5))
+        dvdy_m = strain[1, j, i] / rho[j, i]
+        shear_m = strain[2, j, i] / rho[j, i]
+        dvdy_fd = 0.5 * (u[1, j + 1, i] - u[1, j - 1, i])
+        shear_fd = 0.5 * (u[0, j + 1, i] - u[0, j - 1, i]) + 0.5 * (u[1, j, i + 1] - u[1, j, i - 1])
+        out[name] = (float(dvdy_m), float(dvdy_fd), float(shear_m), float(shear_fd))
+    return out
 
 
 def stream_function(u):

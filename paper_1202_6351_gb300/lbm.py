@@ -51,6 +51,7 @@ SIGNATURES = {
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_set_force": (_i, [_vp, _dp]),
     "lbm_set_omegas": (_i, [_vp, _dp]),
+    "lbm_set_graph_steps": (_i, [_vp, _i]),
     "lbm_set_variant": (_i, [_vp, _i]),
     "lbm_tune": (_i, [_vp, _i, C.POINTER(C.c_float)]),
     "lbm_set_force_field": (_i, [_vp, _vp, _i]),
@@ -237,6 +238,10 @@ class Lattice:
 
     def set_omegas(self, omegas):
         _check(self.lib.lbm_set_omegas(self.h, _darr(omegas, 6)))
+
+    def set_graph_steps(self, steps):
+        _check(self.lib.lbm_set_graph_steps(self.h, int(steps)))
+        return self
 
     def set_variant(self, variant):
         _check(self.lib.lbm_set_variant(self.h, int(variant)))

@@ -48,3 +48,44 @@ def test_stability_ordering_of_table_IV():
                                                                                   th[lbm.CASCADED]))
     assert th[lbm.BGK] < th[lbm.RAWMRT] < th[lbm.CASCADED]
     assert 8.0 <= th[lbm.BGK] <= 25.0
+
+
+@pytest.mark.parametrize("re", [100, 1000])
+def test_strain_rate_from_moments_agrees_with_finite_differences(re):
+    """Sec. IV-C, Table III: the strain rate from local non-equilibrium moments
+    (Eq. 28-30) agrees with central differences of the velocity at the five
+    probe points (the paper: within 2 %)."""
+    rho, u, strain, steps = X.cavity_steady(257, re, fields=True)
+    pts = X.strain_at_points(rho, u, strain)
+    scale = max(max(abs(v[1]), abs(v[3])) for v in pts.values())
+    for name, (dm, dfd, sm, sfd) in pts.items():
+        print(f"Re {re} point {name}: dv/dy {dm:.4e} (moments) {dfd:.4e} (FD); "
+              f"du/dy+dv/dx {sm:.4e} (moments) {sfd:.4e} (FD)")
+        assert abs(dm - dfd) <= 0.02 * max(abs(dfd), 0.1 * scale)
+        assert abs(sm - sfd) <= 0.02 * max(abs(sfd), 0.1 * scale)
+
+
+def test_taylor_green_strain_rate_converges_at_second_order_on_the_gpu():
+    """Sec. III-B: S_xx from the non-equilibrium moments falls as N^-2 against
+    Eq. 41 under diffusive scaling (FP64 storage, one decay time)."""
+    import math
+
+    import oracle as O
+    from paper_1202_6351_gb300 import workloads
+
+    om = 1.6
+    nu = O.nu_from_omega(om)
+    errs = []
+    for n in (32, 64, 128):
+        u0 = workloads.diffusive_u0(n)
+        steps = int(round(O.taylor_green_decay_time(n, nu)))
+        rho0, u_init = workloads.taylor_green_init(n, u0)
+        with lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), store=lbm.F64) as L:
+            L.init(rho0, u_init).step(steps)
+            rho, _ = L.macros()
+            sxx = L.strain()[0] / rho
+        _, _, sa = O.taylor_green(n, u0, nu, steps)
+        errs.append(float(np.sqrt(((sxx - sa) ** 2).sum() / (sa ** 2).sum())))
+    slopes = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    print("S_xx errors", errs, "slopes", slopes)
+    assert all(1.9 < s < 2.15 for s in slopes)

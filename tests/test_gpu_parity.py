@@ -353,3 +353,29 @@ def test_tune_keeps_state_and_picks_a_variant():
     np.testing.assert_array_equal(g.get_f(), before)
     assert g.time == 3
     g.close()
+
+
+# ---------------------------------------------------------------- CUDA-graph replay in lbm_step
+
+@pytest.mark.parametrize("store", [lbm.F32, lbm.F16DEV, lbm.F64], ids=["f32", "f16", "f64"])
+def test_graph_replay_is_bitwise_equal_to_single_launches(store):
+    """lbm_step replays chunks of steps from a CUDA graph; the result must not
+    depend on it, also across an odd start, a rate change and a force change
+    (each forces a new capture)."""
+    nx, ny = 70, 45
+    e, wu = EDGES["channel"]
+    rho, u = workloads.random_fields(12, nx, ny, u_amp=0.03, rho_amp=0.01)
+    runs = []
+    for graph_steps in (0, 8):
+        g = lbm.Lattice(nx, ny, OMEGAS, force=(1e-5, 0.0), edges=e, wall_u=wu, store=store)
+        g.set_graph_steps(graph_steps).init(rho, u)
+        g.step(3)     # odd: the next chunk starts with single launches
+        g.step(37)
+        g.set_omegas((1.0, 1.5, 1.5, 1.0, 1.1, 1.0))
+        g.step(20)
+        g.set_force((0.0, 2e-5))
+        g.step(33)
+        assert g.time == 93
+        runs.append(g.get_f())
+        g.close()
+    np.testing.assert_array_equal(runs[0], runs[1])
