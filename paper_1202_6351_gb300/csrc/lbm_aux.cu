@@ -40,14 +40,20 @@ __device__ __forceinline__ void load_any(const Args& a, bool odd, int x, int y, 
     for (int q = 0; q < 9; ++q) d[q] = double(r[q]) * inv;
 }
 
-// Equilibria used to start a run.  Cascaded: the populations whose central
-// moments about u are (rho, 0, 0, rho/3, rho/3, 0, 0, 0, rho/9) (Eq. 10).  Their
-// raw moments factor as rho M_m(ux) M_n(uy) with M_0 = 1, M_1 = u, M_2 = 1/3 + u^2,
-// so f_eq(e) = rho phi(e_x; ux) phi(e_y; uy) with phi(0; u) = 2/3 - u^2 and
-// phi(+-1; u) = (1/3 + u^2 +- u)/2.  Siblings: the 2nd-order polynomial.
-__device__ __forceinline__ double phi(int e, double u) {
-    return e == 0 ? (2.0 / 3.0 - u * u) : 0.5 * (1.0 / 3.0 + u * u + e * u);
-}
+// Equilibria used to start a run, written directly as deviations f_eq - w rho0
+// so that FP32 arithmetic keeps the full precision of small deviations.
+// Cascaded: the populations whose central moments about u are (rho, 0, 0,
+// rho/3, rho/3, 0, 0, 0, rho/9) (Eq. 10).  Their raw moments factor as
+// rho M_m(ux) M_n(uy) with M_0 = 1, M_1 = u, M_2 = 1/3 + u^2, so
+// f_eq(e) = rho phi(e_x; ux) phi(e_y; uy) with phi(0; u) = 2/3 - u^2 and
+// phi(+-1; u) = (1/3 + u^2 +- u)/2.  With phi = w1 + dphi, w1(0) = 2/3,
+// w1(+-1) = 1/6 (w = w1(e_x) w1(e_y)):
+//   f_eq - w rho0 = (rho - rho0) w + rho (w1x dphi_y + dphi_x w1y + dphi_x dphi_y).
+// Siblings: the 2nd-order polynomial, f_eq - w rho0 = w (rho - rho0) + w rho (3 eu + 9/2 eu^2 - 3/2 u^2).
+template <typename R>
+__device__ __forceinline__ R w1(int e) { return e == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0); }
+template <typename R>
+__device__ __forceinline__ R dphi(int e, R u) { return e == 0 ? -u * u : R(0.5) * (u * u + R(e) * u); }
 
 template <int STORE>
 __global__ void init_kernel(const Args a, int model, int force, bool ffield_double, const double* rho,
@@ -58,26 +64,29 @@ __global__ void init_kernel(const Args a, int model, int force, bool ffield_doub
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= a.nx) return;
     const long long n = (long long)y * a.nx + x, p = (long long)a.nx * a.ny;
-    const double r = rho ? rho[n] : a.rho0;
-    const double ux = u ? u[n] : 0.0, uy = u ? u[p + n] : 0.0;
-    double Fx, Fy;
-    node_force_any(a, force, x, y, Fx, Fy, ffield_double);
-    double Sq[9];
-    source<double>(ux, uy, Fx, Fy, Sq);
+    const R dr = R(rho ? rho[n] - a.rho0 : 0.0);
+    const R r = R(a.rho0) + dr;
+    const R ux = R(u ? u[n] : 0.0), uy = R(u ? u[p + n] : 0.0);
+    double Fxd, Fyd;
+    node_force_any(a, force, x, y, Fxd, Fyd, ffield_double);
+    R Sq[9];
+    source<R>(ux, uy, R(Fxd), R(Fyd), Sq);
     T* f = static_cast<T*>(a.f);
     const long long off = (long long)y * a.pitch + x;
-    const double usq = 1.5 * (ux * ux + uy * uy);
+    const R usq = R(1.5) * (ux * ux + uy * uy);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        double feq;
+        R dev;
         if (model == LBM_CASCADED) {
-            feq = r * phi(cx(q), ux) * phi(cy(q), uy);
+            const R ax = w1<R>(cx(q)), ay = w1<R>(cy(q));
+            const R bx = dphi<R>(cx(q), ux), by = dphi<R>(cy(q), uy);
+            dev = dr * (ax * ay) + r * (ax * by + bx * ay + bx * by);
         } else {
-            const double eu = cx(q) * ux + cy(q) * uy;
-            feq = wgt<double>(q) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
+            const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
+            dev = wgt<R>(q) * (dr + r * (R(3) * eu + R(4.5) * eu * eu - usq));
         }
-        const double dev = (feq - wgt<double>(q) * a.rho0) - 0.5 * Sq[q];
-        f[q * a.plane + off] = S::enc(R(dev * S::scale));
+        dev -= R(0.5) * Sq[q];
+        f[q * a.plane + off] = S::enc(dev * R(S::scale));
     }
 }
 
@@ -112,6 +121,29 @@ struct NodeMacros {
     Moments<double> m;
 };
 
+// rho and u of one node in the storage's arithmetic type (FP32 for all but
+// FP64 storage), returned in FP64: rho = rho0 + sum d keeps its precision.
+template <int STORE>
+__device__ __forceinline__ void node_rho_u(const Args& a, bool odd, int force, bool ffd, int x, int y, double& rho,
+                                           double& ux, double& uy) {
+    using R = typename Store<STORE>::R;
+    R d[9];
+    if (odd) load_node<STORE, true, true>(a, x, y, d);
+    else load_node<STORE, false, true>(a, x, y, d);
+    if (Store<STORE>::scale != 1.0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] *= R(1.0 / Store<STORE>::scale);
+    }
+    const Moments<R> m = moments<R>(d, R(a.rho0));
+    double Fx, Fy;
+    node_force_any(a, force, x, y, Fx, Fy, ffd);
+    const R px = m.jx + R(0.5 * Fx), py = m.jy + R(0.5 * Fy);
+    const R rr = R(a.rho0) + m.drho;
+    rho = a.rho0 + double(m.drho);
+    ux = double(px / rr);
+    uy = double(py / rr);
+}
+
 template <int STORE>
 __device__ __forceinline__ NodeMacros node_macros(const Args& a, bool odd, int force, bool ffd, int x, int y) {
     NodeMacros r;
@@ -132,9 +164,10 @@ __global__ void macros_kernel(const Args a, bool odd, int force, bool ffd, doubl
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= a.nx) return;
     const long long n = (long long)y * a.nx + x, p = (long long)a.nx * a.ny;
-    const NodeMacros r = node_macros<STORE>(a, odd, force, ffd, x, y);
-    if (rho) rho[n] = r.rho;
-    if (u) { u[n] = r.ux; u[p + n] = r.uy; }
+    double r, ux, uy;
+    node_rho_u<STORE>(a, odd, force, ffd, x, y, r, ux, uy);
+    if (rho) rho[n] = r;
+    if (u) { u[n] = ux; u[p + n] = uy; }
 }
 
 // Eq. (28)-(30) with the moments of f = f_bar + S/2: sum e_x^2 S = 2 F_x u_x,
