@@ -113,9 +113,10 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
- * on the lattice itself (the state is snapshot and restored, so it is left
- * unchanged) and keeps the faster; ms (may be NULL) receives the time per step
- * of variants 0 and 1 (0 where not run).  Synchronous. */
+ * with each CTA shape (128x2, 256x1, 64x4, 32x8 threads) on the lattice itself
+ * (the state is snapshot and restored, so it is left unchanged) and keeps the
+ * fastest pair; ms (may be NULL) receives the best time per step of variants
+ * 0 and 1 (0 where not run).  Synchronous. */
 int lbm_tune(lbm_t h, int trial_steps, float ms[2]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
@@ -176,9 +177,10 @@ int lbm_set_check(lbm_t h, long every, double mass_rtol);
 /* Number of steps taken since create / init / set_f. */
 long lbm_time(lbm_t h);
 
-/* Layout facts: dims = (nx, ny, pitch, model, store); bytes = device bytes of
- * the population array; state = its device address (for profiling tools). */
-int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state);
+/* Layout facts: dims = (nx, ny, pitch, model, store, kernel variant, CTA
+ * width of the step kernel); bytes = device bytes of the population array;
+ * state = its device address (for profiling tools). */
+int lbm_info(lbm_t h, long dims[7], size_t* bytes, void** state);
 
 /* Algorithmic bytes one lattice update moves for a storage kind: 9 loads and
  * 9 stores of the stored type (144, 72, 36, 36); 0 for an unknown kind. */

@@ -3,6 +3,7 @@
 // Validates arguments, owns the device memory of a lattice, tracks the step
 // counter (whose parity selects the AA-pattern kernel) and turns CUDA failures
 // into status codes with a per-thread message.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -350,6 +351,7 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[2]) {
     const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
     if (ms) ms[0] = ms[1] = 0.f;
     const int nvar = h->store == LBM_F64 ? 1 : 2;
+    static const int widths[4] = {128, 256, 64, 32};  // CTA shapes 128x2, 256x1, 64x4, 32x8
     void* backup = nullptr;
     LBM_CUDA(cudaMallocAsync(&backup, h->state_bytes, h->stream), "tune snapshot allocation");
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -357,23 +359,29 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[2]) {
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     float best = 1e30f;
-    int best_v = 0;
+    int best_v = 0, best_w = 128;
     for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
-        h->a.variant = v;
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
-        if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
-        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
-        if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
-        if (e == cudaSuccess) {
-            if (ms) ms[v] = t / steps;
-            if (t < best) { best = t; best_v = v; }
-            e = cudaMemcpyAsync(h->state, backup, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        float best_of_v = 1e30f;
+        for (int wi = 0; wi < 4 && e == cudaSuccess; ++wi) {
+            h->a.variant = v;
+            h->a.block_x = widths[wi];
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+            if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
+            for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+            if (e == cudaSuccess) {
+                best_of_v = std::min(best_of_v, t / steps);
+                if (t < best) { best = t; best_v = v; best_w = widths[wi]; }
+                e = cudaMemcpyAsync(h->state, backup, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+            }
         }
+        if (ms && e == cudaSuccess) ms[v] = best_of_v;
     }
     h->a.variant = best_v;
+    h->a.block_x = best_w;
     cudaFreeAsync(backup, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (t0) cudaEventDestroy(t0);
@@ -575,10 +583,11 @@ int lbm_set_check(lbm_t h, long every, double mass_rtol) {
 
 long lbm_time(lbm_t h) { return h ? h->t : -1; }
 
-int lbm_info(lbm_t h, long dims[5], size_t* bytes, void** state) {
+int lbm_info(lbm_t h, long dims[7], size_t* bytes, void** state) {
     if (!h) return fail(LBM_EINVAL, "null lattice handle");
     if (dims) {
         dims[0] = h->a.nx; dims[1] = h->a.ny; dims[2] = h->a.pitch; dims[3] = h->model; dims[4] = h->store;
+        dims[5] = h->a.variant; dims[6] = h->a.block_x > 0 ? h->a.block_x : lbm::kStepBX;
     }
     if (bytes) *bytes = h->state_bytes;
     if (state) *state = h->state;

@@ -95,6 +95,7 @@ struct Args {
     double rho0;
     double scale;             // storage scale of the deviations (Store<>::scale)
     int variant;              // 0: one node per thread; 1: two rows per thread, packed FP32x2 (FP32 arithmetic)
+    int block_x;              // CTA width of the step kernels (CTA height = 256 / block_x); 0 means 128
     // The constants the step kernels use, converted once on the host into both
     // arithmetic types (GB300's FP64 rate is far too low for per-thread
     // conversions or divisions): omega_3/12, omega_4/4 .. omega_8/4 (Eq. 17-22),

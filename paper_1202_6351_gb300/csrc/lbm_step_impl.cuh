@@ -15,8 +15,8 @@ namespace lbm {
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
-    const int x = blockIdx.x * kStepBX + threadIdx.x;
-    const int y = blockIdx.y * kStepBY + threadIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
 }
@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
 // arithmetic; a pair that touches a wall edge takes the per-node wall path.
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 __global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const Args a) {
-    const int x = blockIdx.x * kStepBX + threadIdx.x;
-    const int y = 2 * (blockIdx.y * kStepBY + threadIdx.y);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = 2 * (blockIdx.y * blockDim.y + threadIdx.y);
     if (x >= a.nx || y >= a.ny) return;
     const bool two = y + 1 < a.ny;
     if (WALLS && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y + 1 >= a.ny - 1))) {
@@ -39,16 +39,17 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const A
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
-    const dim3 block(kStepBX, kStepBY);
+    const int bx = a.block_x > 0 ? a.block_x : kStepBX, by = (kStepBX * kStepBY) / bx;
+    const dim3 block(bx, by);
     if constexpr (STORE != LBM_F64) {
         if (a.variant == 1) {
             const int rows = (a.ny + 1) / 2;
-            const dim3 grid((a.nx + kStepBX - 1) / kStepBX, (rows + kStepBY - 1) / kStepBY);
+            const dim3 grid((a.nx + bx - 1) / bx, (rows + by - 1) / by);
             step_kernel_pair<MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
             return cudaGetLastError();
         }
     }
-    const dim3 grid((a.nx + kStepBX - 1) / kStepBX, (a.ny + kStepBY - 1) / kStepBY);
+    const dim3 grid((a.nx + bx - 1) / bx, (a.ny + by - 1) / by);
     step_kernel<MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -173,12 +173,12 @@ def lbm_set_check(h, every: int, mass_rtol: float):
 
 
 def lbm_info(h):
-    dims = (C.c_long * 5)()
+    dims = (C.c_long * 7)()
     nbytes = C.c_size_t()
     state = C.c_void_p()
     _check(load_library().lbm_info(h, dims, C.byref(nbytes), C.byref(state)))
     return {"nx": dims[0], "ny": dims[1], "pitch": dims[2], "model": dims[3], "store": dims[4],
-            "bytes": nbytes.value, "state": state.value}
+            "variant": dims[5], "block_x": dims[6], "bytes": nbytes.value, "state": state.value}
 
 
 def lbm_bytes_per_update(store: int) -> int:
