@@ -113,7 +113,7 @@ struct DevBuf {
 // True if two argument blocks launch the same step kernels on the same data.
 bool same_launch(const Args& x, const Args& y) {
     if (x.f != y.f || x.plane != y.plane || x.nx != y.nx || x.ny != y.ny || x.pitch != y.pitch) return false;
-    if (x.ffield != y.ffield || x.variant != y.variant || x.scale != y.scale) return false;
+    if (x.ffield != y.ffield || x.variant != y.variant || x.block_x != y.block_x || x.scale != y.scale) return false;
     for (int k = 0; k < 4; ++k)
         if (x.wall[k] != y.wall[k] || x.wallx[k] != y.wallx[k] || x.wally[k] != y.wally[k] ||
             x.wallxf[k] != y.wallxf[k] || x.wallyf[k] != y.wallyf[k])
