@@ -20,6 +20,12 @@
  *     equal their relaxation targets.
  *   - the moving-wall correction of Sec. III-C is applied along the wall:
  *     f_b(x) = f~_bbar(x) + 6 w_b rho_w (e_b . U_wall), with rho_w = rho_0.
+ *   - a diagonal link that crosses the corner point where two walls meet
+ *     (e.g. the lid and a side wall of the cavity) is bounced back with no
+ *     moving-wall term.  Sec. III-C lists the lid's incoming directions
+ *     without saying which wall owns such a link; giving it the lid term
+ *     makes the cavity converge at first order, not the second order that
+ *     Sec. III-C reports for it.
  *   - initial populations are the transformed equilibrium of Eq. (12),
  *     i.e. f_bar = f_eq(rho, u) - S/2.
  *   - SRT-BGK and raw-moment MRT are only named by the paper; they are
@@ -356,8 +362,8 @@ void ONAME(oracle_collide_all)(const oracle_lattice* L, const real* f, real* pos
  * leaving the lattice through a periodic edge re-enters on the other side; one
  * leaving through a wall is reflected into the opposite direction at the same
  * node (half-way bounce-back, Sec. III-A), with the moving-wall correction of
- * Sec. III-C.  A link leaving through a south/north edge is decided by that
- * edge even when it also leaves in x (corner links hit the lid first). */
+ * Sec. III-C.  A diagonal link that leaves through the corner point of two
+ * walls is reflected with no moving-wall term (reading in the header). */
 void ONAME(oracle_stream_all)(const oracle_lattice* L, const real* post, real* f)
 {
     const int nx = L->nx, ny = L->ny;
@@ -369,15 +375,14 @@ void ONAME(oracle_stream_all)(const oracle_lattice* L, const real* post, real* f
                 int dx = x + EX[a], dy = y + EY[a];
                 const int yw = dy < 0 ? 2 : (dy >= ny ? 3 : -1);
                 const int xw = dx < 0 ? 0 : (dx >= nx ? 1 : -1);
-                int wall = -1;
-                if (yw >= 0 && L->edge[yw] != ORACLE_PERIODIC)
-                    wall = yw;
-                else if (xw >= 0 && L->edge[xw] != ORACLE_PERIODIC)
-                    wall = xw;
+                const int ywall = yw >= 0 && L->edge[yw] != ORACLE_PERIODIC;
+                const int xwall = xw >= 0 && L->edge[xw] != ORACLE_PERIODIC;
+                const int corner = ywall && xwall;
+                const int wall = ywall ? yw : (xwall ? xw : -1);
                 if (wall >= 0) {
                     const int b = OPP[a];
                     real corr = 0;
-                    if (L->edge[wall] == ORACLE_MOVING_WALL) {
+                    if (!corner && L->edge[wall] == ORACLE_MOVING_WALL) {
                         /* tangential wall velocity: along x on S/N, along y on W/E */
                         const real Ux = (wall >= 2) ? L->wall_u[wall] : 0.0;
                         const real Uy = (wall >= 2) ? 0.0 : L->wall_u[wall];

@@ -82,13 +82,16 @@ inline double store_scale(int store) { return store == LBM_F16DEV ? Store<LBM_F1
 // Plain-old-data, passed by value to every kernel.
 // Index of the per-launch constants in Args::kf / Args::kd.
 enum : int { K_C3 = 0, K_W3 = 6, K_RHO0 = 12, K_FX = 13, K_FY = 14, K_SCALE = 15, K_COUNT = 16 };
+// Slot of the wall-term arrays used by a link that enters through a corner
+// where two walls meet: it is bounced back with no wall-motion term.
+enum : int { kCorner = 4 };
 
 struct Args {
     void* f;                  // populations [9][ny][pitch] of the stored type
     long long plane;          // pitch * ny
     int nx, ny, pitch;
     int wall[4];              // 1 if the edge (W, E, S, N) is a wall
-    double wallx[4], wally[4];// 6 rho_w U_wall (x, y components) per edge
+    double wallx[5], wally[5];// 6 rho_w U_wall (x, y components) per edge; [kCorner] = 0
     double om[6];             // omega_3 .. omega_8
     double F[2];              // uniform body force
     const void* ffield;       // per-node force [2][ny][nx] (Real), or null
@@ -102,11 +105,14 @@ struct Args {
     // omega_3 .. omega_8, and rho0, F_x, F_y and the wall terms in stored units.
     float kf[K_COUNT];
     double kd[K_COUNT];
-    float wallxf[4], wallyf[4];
+    float wallxf[5], wallyf[5];
 };
 
-// Fill Args::kf, kd, wallxf, wallyf from om, rho0, F, wallx, wally.
+// Fill Args::kf, kd, wallxf, wallyf from om, rho0, F, wallx, wally (and zero
+// the corner slot).
 inline void prepare_constants(Args& a) {
+    a.wallx[kCorner] = 0.0;
+    a.wally[kCorner] = 0.0;
     a.kd[K_C3] = a.om[0] / 12.0;
     for (int k = 1; k < 6; ++k) a.kd[K_C3 + k] = a.om[k] / 4.0;
     for (int k = 0; k < 6; ++k) a.kd[K_W3 + k] = a.om[k];
@@ -115,7 +121,7 @@ inline void prepare_constants(Args& a) {
     a.kd[K_FY] = a.F[1] * a.scale;
     a.kd[K_SCALE] = a.scale;
     for (int k = 0; k < K_COUNT; ++k) a.kf[k] = float(a.kd[k]);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         a.wallxf[k] = float(a.wallx[k] * a.scale);
         a.wallyf[k] = float(a.wally[k] * a.scale);
     }
@@ -143,13 +149,18 @@ struct Coef {
 
 // ---------------------------------------------------------------- walls
 // Wall through which the link arriving at (x, y) in direction q comes from
-// outside the lattice, or -1.  South/north first (corner links hit the lid).
+// outside the lattice, or -1.  A diagonal link whose path crosses the corner
+// point of two walls belongs to neither: it returns kCorner (plain bounce-back,
+// no wall-motion term).  With the lid term on that link instead, the
+// lid-driven cavity of Sec. III-C converges at first order only; without it,
+// at the second order the paper reports there.
 __device__ __forceinline__ int incoming_wall(const Args& a, int q, int x, int y) {
-    if (cy(q) == 1 && y == 0 && a.wall[LBM_SOUTH]) return LBM_SOUTH;
-    if (cy(q) == -1 && y == a.ny - 1 && a.wall[LBM_NORTH]) return LBM_NORTH;
-    if (cx(q) == 1 && x == 0 && a.wall[LBM_WEST]) return LBM_WEST;
-    if (cx(q) == -1 && x == a.nx - 1 && a.wall[LBM_EAST]) return LBM_EAST;
-    return -1;
+    int wy = -1, wx = -1;
+    if (cy(q) == 1 && y == 0 && a.wall[LBM_SOUTH]) wy = LBM_SOUTH;
+    if (cy(q) == -1 && y == a.ny - 1 && a.wall[LBM_NORTH]) wy = LBM_NORTH;
+    if (cx(q) == 1 && x == 0 && a.wall[LBM_WEST]) wx = LBM_WEST;
+    if (cx(q) == -1 && x == a.nx - 1 && a.wall[LBM_EAST]) wx = LBM_EAST;
+    return wy >= 0 ? (wx >= 0 ? int(kCorner) : wy) : wx;
 }
 // Moving-wall term for a population entering in direction q through wall w.
 template <typename R>

@@ -88,7 +88,8 @@ def stream_pull_reference(post, edges, wall_u, rho_w=1.0):
     form with explicit loops: f_a(x) = post_a(x - e_a) if that node exists (after
     periodic wrap), else post_abar(x) plus the moving-wall term
     6 w_a rho_w (e_a . U_wall).  A source outside in y is decided by the S/N
-    edge first."""
+    edge first; a source outside past both a S/N wall and a W/E wall (the
+    corner point) takes no moving-wall term."""
     nine, ny, nx = post.shape
     w = weights()
     opp = [int(np.where((EX == -EX[a]) & (EY == -EY[a]))[0][0]) for a in range(9)]
@@ -104,9 +105,10 @@ def stream_pull_reference(post, edges, wall_u, rho_w=1.0):
                     wall = yw
                 elif xw >= 0 and edges[xw] != 0:
                     wall = xw
+                corner = yw >= 0 and edges[yw] != 0 and xw >= 0 and edges[xw] != 0
                 if wall >= 0:
                     corr = 0.0
-                    if edges[wall] == 2:
+                    if edges[wall] == 2 and not corner:
                         U = (wall_u[wall], 0.0) if wall >= 2 else (0.0, wall_u[wall])
                         corr = 6.0 * w[a] * rho_w * (EX[a] * U[0] + EY[a] * U[1])
                     out[a, y, x] = post[opp[a], y, x] + corr

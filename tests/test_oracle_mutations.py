@@ -38,6 +38,10 @@ def _conservation():
         T.test_collision_conserves_mass_and_adds_force(m)
 
 
+def _corner_symmetry():
+    T.test_cavity_is_equivariant_under_a_quarter_turn(O.CASCADED)
+
+
 def _unit_rates():
     T.test_unit_rates_give_the_cascaded_equilibrium()
 
@@ -59,6 +63,8 @@ MUTATIONS = [
     ("wrong rest target of xxyy", "(1.0 / 9.0) * rho + 3.0", "(1.0 / 3.0) * rho + 3.0", _unit_rates),
     ("lid correction with the wrong sign", "corr = 6.0 * W[b]", "corr = -6.0 * W[b]", _couette),
     ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
+    ("lid term on the links through a corner", "if (!corner && L->edge[wall] == ORACLE_MOVING_WALL)",
+     "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),
     ("transposed K in the raw-MRT projection", "m += KMAT[a][b] * fb[a];", "m += KMAT[b][a] * fb[a];",
      _mrt),
     ("omega_3 used for the deviatoric kernel", "(w4 / 4.0) * (rho * (ux * ux - uy * uy)",
