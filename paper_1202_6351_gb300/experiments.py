@@ -6,8 +6,11 @@
   the stream function psi(x, y) = sum of u along y from the bottom wall.
 * :func:`max_stable_cell_reynolds` finds, for one collision model and grid,
   the largest cell Reynolds number Re_c = U dx / nu at which the cavity stays
-  bounded (Sec. V, Table IV), running many viscosities side by side in one
-  batched launch per step.
+  stable (Sec. V, Table IV), running many viscosities side by side in one
+  batched launch per step; :func:`max_stable_lid_velocity` does the same for
+  the lid speed on a fixed coarse grid at fixed viscosity (Sec. V).
+* :func:`secondary_vortex` locates the corner vortices of Table II and
+  :func:`cavity_convergence` runs the grid-convergence study of Sec. III-C.
 
 All lattice work goes through the C ABI (:mod:`paper_1202_6351_gb300.lbm`);
 this module only sets parameters and post-processes fields with numpy.
@@ -30,12 +33,13 @@ def cavity_omega(n, re, U=0.1):
 
 
 def cavity_steady(n, re, model=lbm.CASCADED, store=lbm.F32, U=0.1, tol=1e-7, check=1000, max_steps=2_000_000,
-                  other_rate=1.0, fields=False):
+                  other_rate=1.0, fields=False, nu=None):
     """Run from rest until max |u(t) - u(t - check)| < tol (per `check` steps).
+    The viscosity is nu = U (n - 1)/re unless `nu` is given.
     Returns (u[2, n, n], steps), or with fields=True (rho, u, strain[3, n, n], steps)
     where strain holds (d_x j_x, d_y j_y, d_x j_y + d_y j_x) from the
     non-equilibrium moments (Eq. 28-30)."""
-    om = cavity_omega(n, re, U)
+    om = cavity_omega(n, re, U) if nu is None else 1.0 / (3.0 * nu + 0.5)
     rates = (other_rate, om, om, other_rate, other_rate, other_rate)
     with lbm.Lattice(n, n, rates, edges=CAVITY_EDGES, wall_u=(0, 0, 0, U), model=model, store=store) as L:
         L.init()
@@ -100,42 +104,174 @@ def vortex_centre(u):
     return ((i + di + 0.5) / n, (j + dj + 0.5) / n)
 
 
-def max_stable_cell_reynolds(model, n, U=0.1, cell_res=None, convective_times=20.0, store=lbm.F32):
-    """Largest Re_c = U / nu in `cell_res` (default: 48 values log-spaced in [4, 400])
-    below which every candidate n x n cavity stays bounded for
-    `convective_times` x n / U steps; all candidates run in one batch.
+def _stable(u):
+    """A run is stable unless it blew up: every velocity finite and within the
+    range D2Q9 populations can carry (|u_x|, |u_y| <= 1 needs no negative
+    population).  Returns (stable, max |u|)."""
+    if not np.isfinite(u).all():
+        return False, float("inf")
+    umax = float(np.abs(u).max())
+    return umax <= 1.0, umax
 
-    Sec. V calls a run unstable when its error grows rapidly or exponentially;
-    here a run is stable if every velocity stays finite and below the lattice
-    sound speed c_s = 1/sqrt(3).  (Above some Re_c the cascaded and MRT runs keep
-    a bounded hot spot of a few times U at the lid corners without blowing up;
-    a bound of a few U would call those unstable.)
-    Returns (threshold, list of (Re_c, stable, max |u|))."""
-    if cell_res is None:
-        cell_res = np.exp(np.linspace(math.log(4.0), math.log(400.0), 48))
+
+def _cavity_sweep(model, n, cases, steps, store):
+    """Run one n x n cavity per (nu, U) in `cases` side by side in one batched
+    launch per step for `steps` steps; returns [(stable, max |u|)]."""
     lattices = []
-    for rc in cell_res:
-        nu = U / rc
+    for nu, U in cases:
         om = 1.0 / (3.0 * nu + 0.5)
         L = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), edges=CAVITY_EDGES, wall_u=(0, 0, 0, U), model=model,
                         store=store)
         L.init()
         lattices.append(L)
-    steps = int(convective_times * n / U)
     steps += steps % 2
     with lbm.Batch(lattices) as B:
         B.step(steps)
         B.sync()
-    result = []
-    cs = 1.0 / math.sqrt(3.0)
-    for rc, L in zip(cell_res, lattices):
+    out = []
+    for L in lattices:
         _, u = L.macros()
-        umax = float(np.abs(u).max()) if np.isfinite(u).all() else float("inf")
-        result.append((float(rc), umax < cs, umax))
+        out.append(_stable(u))
         L.close()
+    return out
+
+
+def _threshold(values, flags):
+    """Largest candidate below which every candidate (in increasing order) was stable."""
     threshold = 0.0
-    for rc, ok, _ in result:  # largest Re_c below which every candidate was stable
+    for v, ok in zip(values, flags):
         if not ok:
             break
-        threshold = rc
-    return threshold, result
+        threshold = v
+    return threshold
+
+
+def max_stable_cell_reynolds(model, n, U=0.1, cell_res=None, convective_times=20.0, store=lbm.F32):
+    """Largest Re_c = U / nu in `cell_res` (default: 48 values log-spaced in [4, 400])
+    below which every candidate n x n cavity stays stable for
+    `convective_times` x n / U steps (Sec. V, Table IV: the lid speed is fixed
+    and the viscosity lowered); all candidates run in one batch.
+
+    Sec. V calls a run unstable when its error grows rapidly or becomes
+    exponentially large; here a run is unstable when it blows up (a
+    non-finite velocity, or one beyond what the lattice can carry).  Above
+    some Re_c the cascaded runs keep a bounded hot spot near the lid corners
+    with velocities close to the lattice sound speed without blowing up; they
+    count as stable.
+    Returns (threshold, list of (Re_c, stable, max |u|))."""
+    if cell_res is None:
+        cell_res = np.exp(np.linspace(math.log(4.0), math.log(400.0), 48))
+    cell_res = [float(rc) for rc in cell_res]
+    res = _cavity_sweep(model, n, [(U / rc, U) for rc in cell_res], int(convective_times * n / U), store)
+    result = [(rc, ok, umax) for rc, (ok, umax) in zip(cell_res, res)]
+    return _threshold(cell_res, [ok for _, ok, _ in result]), result
+
+
+def max_stable_lid_velocity(model, nu, n=26, lid_u=None, steps=50_000, store=lbm.F32):
+    """Sec. V's alternative test: on a fixed coarse n x n cavity (26 x 26) at a
+    fixed viscosity, the largest lid speed in `lid_u` (default: 40 values
+    log-spaced in [0.005, 0.8]) below which every candidate stays stable for
+    `steps` steps (50,000).  Returns (threshold, list of (U, stable, max |u|))."""
+    if lid_u is None:
+        lid_u = np.exp(np.linspace(math.log(0.005), math.log(0.8), 40))
+    lid_u = [float(U) for U in lid_u]
+    res = _cavity_sweep(model, n, [(nu, U) for U in lid_u], steps, store)
+    result = [(U, ok, umax) for U, (ok, umax) in zip(lid_u, res)]
+    return _threshold(lid_u, [ok for _, ok, _ in result]), result
+
+
+# Corner regions (in units of L) searched for the counter-rotating secondary
+# vortices of Sec. IV-C, Table II.
+SECONDARY_REGIONS = {"bottom_left": ((0.0, 0.35), (0.0, 0.35)), "bottom_right": ((0.65, 1.0), (0.0, 0.35)),
+                     "top_left": ((0.0, 0.35), (0.65, 1.0))}
+
+
+def secondary_vortex(u, region):
+    """Centre of the secondary (counter-clockwise) vortex in a corner region:
+    the maximum of psi there, refined by parabolas; None if psi has no interior
+    maximum in the region (no such vortex)."""
+    psi = stream_function(u)
+    n = psi.shape[0]
+    (x0, x1), (y0, y1) = SECONDARY_REGIONS[region]
+    i0, i1 = max(1, int(x0 * n)), min(n - 2, int(x1 * n))
+    j0, j1 = max(1, int(y0 * n)), min(n - 2, int(y1 * n))
+    sub = psi[j0:j1 + 1, i0:i1 + 1]
+    jj, ii = np.unravel_index(np.argmax(sub), sub.shape)
+    j, i = j0 + int(jj), i0 + int(ii)
+    if j in (j0, j1) or i in (i0, i1) or psi[j, i] <= 0.0:
+        return None
+    di = _parabola_vertex(-psi[j, i - 1], -psi[j, i], -psi[j, i + 1])
+    dj = _parabola_vertex(-psi[j - 1, i], -psi[j, i], -psi[j + 1, i])
+    return ((i + di + 0.5) / n, (j + dj + 0.5) / n)
+
+
+def centreline_profiles(u):
+    """u along the vertical centre line and v along the horizontal one (odd n:
+    the centre lines pass through nodes), with their node positions in units of L."""
+    n = u.shape[1]
+    c = (n - 1) // 2
+    pos = (np.arange(n) + 0.5) / n
+    return pos, u[0][:, c], u[1][c, :]
+
+
+# Centre-line quantities of the grid-convergence study (Sec. III-C, Figs. on the
+# cavity): velocity components and the strain-rate components dv/dy and
+# du/dy + dv/dx along the vertical (x = L/2) and horizontal (y = L/2) lines.
+CONVERGENCE_QUANTITIES = ("u_vertical", "u_horizontal", "v_vertical", "v_horizontal", "dvdy_vertical",
+                          "dvdy_horizontal", "shear_vertical", "shear_horizontal")
+
+
+def _centre_lines(rho, u, strain, U, n):
+    """The CONVERGENCE_QUANTITIES in units of U (velocities) and U / L (strain
+    rates, from the non-equilibrium moments, Eq. 28-30, divided by rho)."""
+    c = (n - 1) // 2
+    dvdy = strain[1] / rho * (n / U)
+    shear = strain[2] / rho * (n / U)
+    ux, uy = u[0] / U, u[1] / U
+    return {"u_vertical": ux[:, c], "u_horizontal": ux[c, :], "v_vertical": uy[:, c], "v_horizontal": uy[c, :],
+            "dvdy_vertical": dvdy[:, c], "dvdy_horizontal": dvdy[c, :], "shear_vertical": shear[:, c],
+            "shear_horizontal": shear[c, :]}
+
+
+def cavity_convergence(sides=(13, 19, 25, 31, 37, 49), reference=121, re=100.0, u_coarsest=0.1, rel_tol=1e-6,
+                       model=lbm.CASCADED, store=lbm.F64, reference_store=None, reference_steps=None):
+    """Sec. III-C grid convergence at fixed Re under diffusive scaling (U ~ 1/n,
+    nu fixed): relative global errors (Eq. 34, Euclidean norm) of the centre-line
+    quantities CONVERGENCE_QUANTITIES against a finer run, linearly interpolated
+    to the coarse nodes.  With half-way walls the side is L = n, so
+    Re = U n / nu on every grid (a fixed n - 1 would shift Re by O(1/n)).
+
+    Each grid runs until max |du| over 1000 steps is below
+    rel_tol U (n0 / n)^2 (the slowest mode decays at a rate ~ nu / n^2, so this
+    leaves the same residual on every grid); the reference may instead run a
+    fixed `reference_steps` in `reference_store` (an FP32 801^2 run cannot
+    resolve such small changes, and needs no checks).
+    Returns {n: {quantity: error}}."""
+    n0 = sides[0]
+    nu = u_coarsest * n0 / re
+    om = 1.0 / (3.0 * nu + 0.5)
+
+    def run(n, st, steps=None):
+        U = u_coarsest * n0 / n
+        if steps is None:
+            rho, u, strain, _ = cavity_steady(n, re, model=model, store=st, U=U, tol=rel_tol * U * (n0 / n) ** 2,
+                                              max_steps=200_000_000, nu=nu, fields=True)
+        else:
+            with lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), edges=CAVITY_EDGES, wall_u=(0, 0, 0, U), model=model,
+                             store=st) as L:
+                L.init()
+                L.step(steps + steps % 2)
+                rho, u = L.macros()
+                strain = L.strain()
+        return (np.arange(n) + 0.5) / n, _centre_lines(rho, u, strain, U, n)
+
+    pr, ref = run(reference, store if reference_store is None else reference_store, reference_steps)
+    out = {}
+    for n in sides:
+        p, q = run(n, store)
+        errs = {}
+        for k in CONVERGENCE_QUANTITIES:
+            qi = np.interp(p, pr, ref[k])
+            errs[k] = float(np.sqrt(((q[k] - qi) ** 2).sum() / (qi ** 2).sum()))
+        out[n] = errs
+    return out

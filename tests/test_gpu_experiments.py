@@ -30,6 +30,14 @@ def test_primary_vortex_centre_matches_table_I(re):
     px, py = table["cascaded"][k]
     print(f"Re {re}: cascaded centre ({xc:.5f}, {yc:.5f}) after {steps} steps; paper ({px}, {py})")
     assert abs(xc - px) < 0.01 and abs(yc - py) < 0.01
+    # Table II: first secondary vortices in the bottom corners (no top-left one below Re 3200)
+    sec = P.PAPER["secondary_vortices"]["cascaded"][str(re)]
+    for region in ("bottom_left", "bottom_right"):
+        got = X.secondary_vortex(u, region)
+        print(f"Re {re}: {region} vortex {got}; paper {sec[region]}")
+        assert got is not None
+        assert abs(got[0] - sec[region][0]) < 0.01 and abs(got[1] - sec[region][1]) < 0.01
+    assert X.secondary_vortex(u, "top_left") is None
     if re == 1000:  # the raw-moment MRT lands on the same centre (the paper: within 0.014 %)
         um, _ = X.cavity_steady(257, re, model=lbm.RAWMRT)
         xm, ym = X.vortex_centre(um)
@@ -39,15 +47,30 @@ def test_primary_vortex_centre_matches_table_I(re):
 
 def test_stability_ordering_of_table_IV():
     """Sec. V, Table IV: the maximum stable cell Reynolds number grows from SRT to
-    raw MRT to cascaded (14.14 / 59.40 / 148.50 at 101^2 in the paper); a run is
-    stable while its velocity stays finite and below c_s."""
+    raw MRT to cascaded (14.14 / 59.40 / 148.50 at 101^2 in the paper; raw MRT
+    3-4 times SRT and cascaded 2-3 times raw MRT); a run is stable unless it
+    blows up within 20 convective times."""
     th = {}
     for model in (lbm.BGK, lbm.RAWMRT, lbm.CASCADED):
         th[model], _ = X.max_stable_cell_reynolds(model, 101)
     print("max stable cell Re at 101^2: SRT %.1f, raw MRT %.1f, cascaded %.1f" % (th[lbm.BGK], th[lbm.RAWMRT],
                                                                                   th[lbm.CASCADED]))
+    assert 12.0 <= th[lbm.BGK] <= 17.0
+    assert th[lbm.RAWMRT] >= 3.0 * th[lbm.BGK]
+    assert th[lbm.CASCADED] >= 1.8 * th[lbm.RAWMRT]
+
+
+def test_max_stable_lid_velocity_on_a_coarse_grid():
+    """Sec. V's alternative test: 26 x 26 cavity, fixed viscosity, largest lid
+    speed stable for 50,000 steps; the cascaded model reaches a considerably
+    higher speed than the other two (here nu = 0.005)."""
+    th = {}
+    for model in (lbm.BGK, lbm.RAWMRT, lbm.CASCADED):
+        th[model], _ = X.max_stable_lid_velocity(model, 0.005)
+    print("max stable lid speed at 26^2, nu 0.005: SRT %.4f, raw MRT %.4f, cascaded %.4f" % (
+        th[lbm.BGK], th[lbm.RAWMRT], th[lbm.CASCADED]))
     assert th[lbm.BGK] < th[lbm.RAWMRT] < th[lbm.CASCADED]
-    assert 8.0 <= th[lbm.BGK] <= 25.0
+    assert th[lbm.CASCADED] >= 1.5 * th[lbm.RAWMRT]
 
 
 @pytest.mark.parametrize("re", [100, 1000])
@@ -89,3 +112,21 @@ def test_taylor_green_strain_rate_converges_at_second_order_on_the_gpu():
     slopes = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     print("S_xx errors", errs, "slopes", slopes)
     assert all(1.9 < s < 2.15 for s in slopes)
+
+
+def test_cavity_grid_convergence_second_order():
+    """Sec. III-C: Re 100 under diffusive scaling, grids 13^2..121^2 against an
+    801^2 run; the relative global errors of the centre-line velocities and
+    strain rates fall at about second order (the paper's fitted slopes: 2.11 /
+    2.19 for u, 2.18 / 2.11 for v, 1.81 / 1.95 for dv/dy, 2.12 / 2.07 for
+    du/dy + dv/dx on the vertical / horizontal centre lines).  The 801^2
+    reference runs 16 M steps in FP32 (about 17 decay times of its slowest
+    mode); the other grids run in FP64 to a steady state."""
+    errs = X.cavity_convergence(sides=(13, 19, 25, 31, 37, 49, 61, 85, 97, 121), reference=801,
+                                reference_store=lbm.F32, reference_steps=16_000_000)
+    ns = sorted(errs)
+    x = np.log(np.array(ns, dtype=float))
+    for k in X.CONVERGENCE_QUANTITIES:
+        slope = -np.polyfit(x, np.log([errs[n][k] for n in ns]), 1)[0]
+        print(k, " ".join(f"{errs[n][k]:.3e}" for n in ns), f"slope {slope:.3f}")
+        assert 1.8 < slope < 2.7, (k, slope)
