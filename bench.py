@@ -56,6 +56,7 @@ def omegas():
 
 STEP_KERNEL_SOURCES = ("include/lbm.h", "paper_1202_6351_gb300/csrc/lbm_device.cuh",
                        "paper_1202_6351_gb300/csrc/lbm_internal.h", "paper_1202_6351_gb300/csrc/lbm_pair.cuh",
+                       "paper_1202_6351_gb300/csrc/lbm_vec.cuh",
                        "paper_1202_6351_gb300/csrc/lbm_step_impl.cuh", "paper_1202_6351_gb300/csrc/lbm_step_f64.cu",
                        "paper_1202_6351_gb300/csrc/lbm_step_f32.cu", "paper_1202_6351_gb300/csrc/lbm_step_bf16.cu",
                        "paper_1202_6351_gb300/csrc/lbm_step_f16.cu")
@@ -374,14 +375,14 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
             "mlups": round(nodes * steps / s / 1e6, 1),
             "frac": round(lbm.lbm_bytes_per_update(st) * nodes * steps / s / 1e9 / peak, 4),
             "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10}
-    # the per-lattice tuner's timings of the two kernel variants on this workload
+    # the per-lattice tuner's timings of the kernel variants on this workload
+    names = ("one_node_per_thread_mlups", "two_rows_packed_fp32x2_mlups", "four_nodes_64bit_mlups")
     tuned = {}
-    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV)):
+    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV), ("bf16", lbm.BF16DEV)):
         L = make(lbm.CASCADED, st)
         ms = L.tune(100)
         L.close()
-        tuned[name] = {"one_node_per_thread_mlups": round(nodes / ms[0] / 1e3, 1),
-                       "two_rows_packed_fp32x2_mlups": round(nodes / ms[1] / 1e3, 1)}
+        tuned[name] = {k: round(nodes / m / 1e3, 1) for k, m in zip(names, ms) if m > 0}
     out["kernel_variants"] = tuned
     for name, model in (("bgk", lbm.BGK), ("rawmrt", lbm.RAWMRT)):
         L = make(model, lbm.F32)
@@ -421,8 +422,9 @@ def run_batch_extras(lbm, torch, np, peak, sp, steps=200):
         nodes += n * n
         nbytes += n * n * lbm.lbm_bytes_per_update(st)
     stream = torch.cuda.current_stream()
-    # per-domain launches
+    # per-domain launches, each lattice in its own tuned kernel variant and CTA shape
     for L in Ls:
+        L.tune(10)
         L.step(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -107,17 +107,26 @@ int lbm_set_force(lbm_t h, const double force[2]);
 int lbm_set_omegas(lbm_t h, const double omegas[6]);
 
 /* Kernel variant of lbm_step for FP32-arithmetic storage (ignored for LBM_F64):
- * 0 = one node per thread (the default); 1 = two rows per thread with packed
- * FP32x2 arithmetic.  Both compute the same update; variant 1 may round
- * differently in the last bit because it fuses multiply-adds explicitly. */
+ * 0 = one node per thread; 1 = two rows per thread with packed FP32x2
+ * arithmetic; 2 (LBM_BF16DEV and LBM_F16DEV only; LBM_F32 runs variant 0) =
+ * four consecutive nodes of a row per thread, each population plane moved
+ * with 64-bit accesses, elements at vector edges exchanged between
+ * neighbouring lanes, and the per-node path where a neighbour wraps or a wall
+ * is near.  The default is 2 for 16-bit stores of at least 2^20 nodes and 0
+ * otherwise (a smaller launch is latency-bound and one node per thread is
+ * faster).
+ * Variants 0 and 2 produce bit-identical states; variant 1 may round
+ * differently in the last bit because it fuses multiply-adds explicitly.
+ * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
+ * variant outside 0..2. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
- * with each CTA shape (128x2, 256x1, 64x4, 32x8 threads) on the lattice itself
- * (the state is snapshot and restored, so it is left unchanged) and keeps the
- * fastest pair; ms (may be NULL) receives the best time per step of variants
- * 0 and 1 (0 where not run).  Synchronous. */
-int lbm_tune(lbm_t h, int trial_steps, float ms[2]);
+ * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads) on
+ * the lattice itself (the state is snapshot and restored, so it is left
+ * unchanged) and keeps the fastest pair; ms (may be NULL) receives the best
+ * time per step of variants 0..2 (0 where not run).  Synchronous. */
+int lbm_tune(lbm_t h, int trial_steps, float ms[3]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own

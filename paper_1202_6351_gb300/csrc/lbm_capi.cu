@@ -259,6 +259,9 @@ int lbm_create(int nx, int ny, const double omegas[6], const double force[2], co
         a.wally[k] = k >= LBM_SOUTH ? 0.0 : 6.0 * rho0 * U;
         h->walls = h->walls || a.wall[k];
     }
+    // Four nodes per thread for large 16-bit lattices (measured fastest there);
+    // below ~1M nodes a launch is latency-bound and one node per thread is faster.
+    a.variant = ((store == LBM_F16DEV || store == LBM_BF16DEV) && (long long)nx * ny >= (1LL << 20)) ? 2 : 0;
     lbm::prepare_constants(a);
     h->state_bytes = 9 * (size_t)a.plane * elem_size(store);
     cudaError_t e = cudaMalloc(&h->state, h->state_bytes);
@@ -338,19 +341,24 @@ int lbm_set_graph_steps(lbm_t h, int steps) {
     return LBM_OK;
 }
 
+// Variants the storage kind admits: 0 for FP64, 0-1 for FP32, 0-2 for 16-bit.
+static int variant_count(int store) {
+    return store == LBM_F64 ? 1 : (store == LBM_F32 ? 2 : 3);
+}
+
 int lbm_set_variant(lbm_t h, int variant) {
     CHECK_HANDLE(h);
-    if (variant != 0 && variant != 1) return fail(LBM_EINVAL, "variant must be 0 or 1");
-    h->a.variant = h->store == LBM_F64 ? 0 : variant;
+    if (variant < 0 || variant > 2) return fail(LBM_EINVAL, "variant must be 0, 1 or 2");
+    h->a.variant = variant < variant_count(h->store) ? variant : 0;
     return LBM_OK;
 }
 
-int lbm_tune(lbm_t h, int trial_steps, float ms[2]) {
+int lbm_tune(lbm_t h, int trial_steps, float ms[3]) {
     CHECK_HANDLE(h);
     if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1");
     const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
-    if (ms) ms[0] = ms[1] = 0.f;
-    const int nvar = h->store == LBM_F64 ? 1 : 2;
+    if (ms) ms[0] = ms[1] = ms[2] = 0.f;
+    const int nvar = variant_count(h->store);
     static const int widths[4] = {128, 256, 64, 32};  // CTA shapes 128x2, 256x1, 64x4, 32x8
     void* backup = nullptr;
     LBM_CUDA(cudaMallocAsync(&backup, h->state_bytes, h->stream), "tune snapshot allocation");

@@ -1,7 +1,9 @@
 // lbm_step_impl.cuh -- the fused D2Q9 stream-and-collide kernel, instantiated
 // once per storage type by lbm_step_<store>.cu.
 //
-// One thread per node: AA-pattern load of the nine populations (a1, a2),
+// One thread per node (variant 0; variant 1 takes two rows per thread with
+// packed FP32x2 arithmetic, variant 2 four nodes of a row per thread with
+// 64-bit accesses for 16-bit stores): AA-pattern load of the nine populations (a1, a2),
 // decode to FP32/FP64 deviations (a3), macroscopic fields (a4, Eq. 26-27),
 // raw moments (a5, Eq. 15), source (a6, Eq. 13-14), cascaded kernel g3..g8
 // (a7, Eq. 17-22) or a sibling collision, back-transform (a8, Eq. 25), encode
@@ -10,6 +12,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_pair.cuh"
+#include "lbm_vec.cuh"
 
 namespace lbm {
 
@@ -37,10 +40,51 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const A
     step_pair<MODEL, STORE, ODD, FORCE>(a, x, y, two);
 }
 
+// N nodes of a row per thread (16-bit stores, no per-node force field);
+// vectors that need a wrapped or wall neighbour take the per-node path.
+// The CTA is bx x by threads with bx a multiple of 32, so the lanes of a warp
+// hold consecutive vectors of one row (step_vec exchanges elements between
+// neighbouring lanes on odd steps).
+template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+__global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_vec(const Args a) {
+    const int x0 = N * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool inside = x0 < a.nx && y < a.ny;
+    const bool vec = inside && (ODD ? (x0 >= N && x0 + N < a.nx && (!WALLS || (y > 0 && y < a.ny - 1)))
+                                    : (x0 + N <= a.nx));
+    const unsigned vmask = ODD ? __ballot_sync(0xffffffffu, vec) : 0u;
+    if (vec) {
+        step_vec<N, MODEL, STORE, ODD, FORCE>(a, x0, y, vmask, threadIdx.x & 31);
+    } else if (inside) {
+        const int x1 = min(x0 + N, a.nx);
+        for (int x = x0; x < x1; ++x) step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
+    }
+}
+
+// CTA of bx x (256 / bx) threads, bx halved (down to 32) while half of it still
+// covers the `width` threads a row needs, so narrow lattices leave no threads idle.
+static inline dim3 fit_block(int bx, int width) {
+    if (bx % 32 != 0 || bx < 32 || bx > kStepBX * kStepBY) bx = kStepBX;  // lanes of a warp share a row
+    while (bx > 32 && bx / 2 >= width) bx /= 2;
+    return dim3(bx, (kStepBX * kStepBY) / bx);
+}
+
+template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+static cudaError_t launch_vec(const Args& a, cudaStream_t s) {
+    const int vecs = (a.nx + N - 1) / N;
+    const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, vecs);
+    const dim3 grid((vecs + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
+    step_kernel_vec<N, MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
-    const int bx = a.block_x > 0 ? a.block_x : kStepBX, by = (kStepBX * kStepBY) / bx;
-    const dim3 block(bx, by);
+    if constexpr ((STORE == LBM_F16DEV || STORE == LBM_BF16DEV) && FORCE != 2) {
+        if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS>(a, s);
+    }
+    const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
+    const int bx = block.x, by = block.y;
     if constexpr (STORE != LBM_F64) {
         if (a.variant == 1) {
             const int rows = (a.ny + 1) / 2;

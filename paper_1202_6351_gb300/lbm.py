@@ -248,10 +248,11 @@ class Lattice:
         return self
 
     def tune(self, trial_steps=20):
-        """Time the kernel variants, keep the faster; returns ms per step of variants 0 and 1."""
-        ms = (C.c_float * 2)()
+        """Time the kernel variants and CTA shapes, keep the fastest; returns the
+        best ms per step of variants 0..2 (0.0 where the storage has no such variant)."""
+        ms = (C.c_float * 3)()
         _check(self.lib.lbm_tune(self.h, int(trial_steps), ms))
-        return ms[0], ms[1]
+        return tuple(ms)
 
     def set_force_field(self, fxy):
         if fxy is None:
