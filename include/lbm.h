@@ -139,7 +139,11 @@ int lbm_set_force_field(lbm_t h, const double* fxy, int on_device);
  * (rho, u).  The cascaded model uses the equilibrium whose central moments are
  * those of Eq. (10); BGK and raw MRT the second-order polynomial one.
  * rho [ny][nx] may be NULL (rho0 everywhere), u [2][ny][nx] may be NULL (rest).
- * Resets the step counter to 0.  _device: device pointers. */
+ * Resets the step counter to 0.  _device: device pointers.  Host buffers in
+ * page-locked memory mapped into the device address space (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister) are read by the kernel in place; other
+ * host buffers are copied to a device staging buffer first.  Either way the
+ * call is synchronous and the buffers must hold the sizes above. */
 int lbm_init(lbm_t h, const double* rho, const double* u);
 int lbm_init_device(lbm_t h, const double* rho, const double* u);
 
@@ -157,7 +161,9 @@ int lbm_step(lbm_t h, long n);
 int lbm_set_graph_steps(lbm_t h, int steps);
 
 /* Density [ny][nx] and velocity [2][ny][nx] of Eq. (26)-(27) at the current
- * time; either pointer may be NULL.  Host pointers: synchronous. */
+ * time; either pointer may be NULL.  Host pointers: synchronous; mapped
+ * page-locked buffers (as for lbm_init) are written by the kernel in place,
+ * other host buffers through a device staging buffer. */
 int lbm_macros(lbm_t h, double* rho, double* u);
 int lbm_macros_device(lbm_t h, double* rho, double* u);
 

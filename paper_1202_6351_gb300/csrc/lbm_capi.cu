@@ -440,9 +440,30 @@ int lbm_init_device(lbm_t h, const double* rho, const double* u) {
     return after_reset(h);
 }
 
+// Address under which the kernels may access a host buffer directly: page-locked
+// memory mapped into the device address space (cudaHostAlloc / cudaMallocHost /
+// cudaHostRegister memory), else nullptr (pageable memory goes through a copy).
+static double* mapped_host(const double* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
+}
+
 int lbm_init(lbm_t h, const double* rho, const double* u) {
     CHECK_HANDLE(h);
     const size_t n = (size_t)nodes(h);
+    const double* mrho = mapped_host(rho);
+    const double* mu = mapped_host(u);
+    if ((rho || u) && (!rho || mrho) && (!u || mu)) {  // the init kernel reads the caller's buffers in place
+        int rc = init_common(h, mrho, mu);
+        if (rc) return rc;
+        LBM_CUDA(cudaStreamSynchronize(h->stream), "init sync");
+        return after_reset(h);
+    }
     DevBuf buf(h->stream);
     double* drho = nullptr;
     double* du = nullptr;
@@ -496,6 +517,14 @@ int lbm_macros(lbm_t h, double* rho, double* u) {
     CHECK_HANDLE(h);
     if (!rho && !u) return LBM_OK;
     const size_t n = (size_t)nodes(h);
+    double* mrho = mapped_host(rho);
+    double* mu = mapped_host(u);
+    if ((!rho || mrho) && (!u || mu)) {  // the macros kernel writes the caller's buffers in place
+        LBM_CUDA(lbm::launch_macros(h->a, h->store, h->t & 1, h->walls, force_mode(h), mrho, mu, h->stream),
+                 "macros kernel");
+        LBM_CUDA(cudaStreamSynchronize(h->stream), "macros sync");
+        return LBM_OK;
+    }
     DevBuf buf(h->stream);
     LBM_CUDA(buf.alloc(3 * n * sizeof(double)), "macros staging");
     double* drho = static_cast<double*>(buf.p);

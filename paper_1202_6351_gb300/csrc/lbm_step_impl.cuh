@@ -45,8 +45,11 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const A
 // The CTA is bx x by threads with bx a multiple of 32, so the lanes of a warp
 // hold consecutive vectors of one row (step_vec exchanges elements between
 // neighbouring lanes on odd steps).
+// Register budget per parity, as measured: the even step keeps all nine planes
+// aligned and spills at 64 registers, so it gets 80 (3 CTAs per SM); the odd
+// step runs faster with more warps at 64 (4 CTAs per SM).
 template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
-__global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_vec(const Args a) {
+__global__ void __launch_bounds__(kStepBX * kStepBY, ODD ? 4 : 3) step_kernel_vec(const Args a) {
     const int x0 = N * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool inside = x0 < a.nx && y < a.ny;

@@ -408,6 +408,47 @@ def test_vector_variants_reduced_precision_bound(store, variant):
     g.close()
 
 
+@pytest.mark.parametrize("store", [lbm.F64, lbm.F32, lbm.F16DEV], ids=["f64", "f32", "f16"])
+def test_init_and_macros_read_and_write_pinned_host_buffers_in_place(store):
+    """lbm_init / lbm_macros access mapped page-locked host buffers from the
+    kernels directly and pageable ones through a staging copy; both paths must
+    give the same state and fields, with NULL for either field."""
+    import torch
+
+    nx, ny = 70, 45
+    e, wu = EDGES["cavity"]
+    rho, u = workloads.random_fields(31, nx, ny, u_amp=0.03, rho_amp=0.01)
+    lib = lbm.load_library()
+    results = []
+    for pinned in (False, True):
+        g = lbm.Lattice(nx, ny, OMEGAS, edges=e, wall_u=wu, store=store)
+        if pinned:
+            rho_h = torch.from_numpy(rho).pin_memory()
+            u_h = torch.from_numpy(u).pin_memory()
+            lbm._check(lib.lbm_init(g.h, rho_h.data_ptr(), u_h.data_ptr()))
+        else:
+            g.init(rho, u)
+        f0 = g.get_f()
+        g.step(7)
+        out_r = torch.zeros((ny, nx), dtype=torch.float64).pin_memory() if pinned else np.zeros((ny, nx))
+        out_u = torch.zeros((2, ny, nx), dtype=torch.float64).pin_memory() if pinned else np.zeros((2, ny, nx))
+        ptr = (lambda t: t.data_ptr()) if pinned else (lambda a: a.ctypes.data)
+        lbm._check(lib.lbm_macros(g.h, ptr(out_r), ptr(out_u)))
+        only_u = torch.zeros((2, ny, nx), dtype=torch.float64).pin_memory() if pinned else np.zeros((2, ny, nx))
+        lbm._check(lib.lbm_macros(g.h, None, ptr(only_u)))
+        if pinned:
+            lbm._check(lib.lbm_init(g.h, None, u_h.data_ptr()))  # rho defaults to rho0
+        else:
+            g.init(None, u)
+        f_rest = g.get_f()
+        g.close()
+        as_np = (lambda t: t.numpy()) if pinned else (lambda a: a)
+        results.append((f0, as_np(out_r).copy(), as_np(out_u).copy(), as_np(only_u).copy(), f_rest))
+    for a, b in zip(results[0], results[1]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(results[1][2], results[1][3])
+
+
 def test_tune_keeps_state_and_picks_a_variant():
     n = 256
     rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
