@@ -244,7 +244,8 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out);
 int lbm_batch_destroy(lbm_batch_t b);
 
 /* Autotuner: times `trial_steps` launches of every tile shape (128x2, 256x1,
- * 64x4, 32x8 nodes per 256-thread CTA), work-list order (lattice by lattice,
+ * 64x4, 32x8 threads per 256-thread CTA, each thread updating one node row or
+ * four node rows of the tile), work-list order (lattice by lattice,
  * largest first; or one tile of each lattice in turn) and scheduling policy
  * (round robin, contiguous chunks, dynamic via an atomic counter) and keeps
  * the fastest.  The lattices' states are snapshot and restored, so tuning
@@ -260,7 +261,7 @@ int lbm_batch_set_graph_steps(lbm_batch_t b, int steps);
 /* Wait for the batch's queued work. */
 int lbm_batch_sync(lbm_batch_t b);
 
-/* cfg = (tile width, tile height, policy, order, grid CTAs, tiles); stream
+/* cfg = (tile width, tile height in nodes, policy, order, grid CTAs, tiles); stream
  * receives the batch's cudaStream_t (for timing with events).  Either may be NULL. */
 int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
 

@@ -11,9 +11,9 @@
 #include "lbm_handle.h"
 
 namespace lbm {
-cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
-cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
-cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
 int batch_blocks_per_sm_cascaded();
 int batch_blocks_per_sm_bgk();
 int batch_blocks_per_sm_rawmrt();
@@ -34,7 +34,7 @@ struct lbm_batch_s {
     int ntiles = 0;
     int* d_counters = nullptr;
     int ncounters = 0;
-    int lbx = 7, policy = lbm::kPolicyRoundRobin, order = 0, grid = 0;
+    int lbx = 7, rows = 1, policy = lbm::kPolicyRoundRobin, order = 0, grid = 0;
     int sms = 0;
     int graph_steps = 100;
     cudaGraphExec_t graph = nullptr;
@@ -47,15 +47,18 @@ constexpr int kShapes[4] = {7, 8, 6, 5};  // log2 of the tile width: 128x2, 256x
 
 int fail(int code, const char* msg) { return lbm::set_error(code, "%s", msg); }
 
-long long tiles_of(const lbm_s* h, int lbx) {
-    const int bx = 1 << lbx, by = lbm::kBatchThreads >> lbx;
+constexpr int kRows[2] = {1, 4};  // node rows per thread
+
+long long tiles_of(const lbm_s* h, int lbx, int rows) {
+    const int bx = 1 << lbx, by = (lbm::kBatchThreads >> lbx) * rows;
     return (long long)((h->a.nx + bx - 1) / bx) * ((h->a.ny + by - 1) / by);
 }
 
-// Work list for tile shape lbx.  order 0: domain after domain, largest domain
+// Work list for tile shape lbx with `rows` node rows per thread (a tile is
+// bx x (256 / bx) * rows nodes).  order 0: domain after domain, largest domain
 // first; order 1: one tile of each domain in turn (largest first).
-std::vector<int> build_tiles(const lbm_batch_s* b, int lbx, int order) {
-    const int bx = 1 << lbx, by = lbm::kBatchThreads >> lbx;
+std::vector<int> build_tiles(const lbm_batch_s* b, int lbx, int rows, int order) {
+    const int bx = 1 << lbx, by = (lbm::kBatchThreads >> lbx) * rows;
     std::vector<int> idx(b->doms.size());
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
@@ -87,8 +90,8 @@ std::vector<int> build_tiles(const lbm_batch_s* b, int lbx, int order) {
     return t;
 }
 
-cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int order) {
-    const std::vector<int> t = build_tiles(b, lbx, order);
+cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int rows, int order) {
+    const std::vector<int> t = build_tiles(b, lbx, rows, order);
     b->ntiles = int(t.size() / 3);
     return cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
 }
@@ -113,13 +116,13 @@ cudaError_t refresh_domains(lbm_batch_s* b) {
 cudaError_t launch(lbm_batch_s* b, int flip, int* counter) {
     switch (b->model) {
         case LBM_CASCADED:
-            return lbm::launch_batch_cascaded(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy,
+            return lbm::launch_batch_cascaded(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy,
                                               counter, b->stream);
         case LBM_BGK:
-            return lbm::launch_batch_bgk(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy, counter,
+            return lbm::launch_batch_bgk(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy, counter,
                                          b->stream);
         default:
-            return lbm::launch_batch_rawmrt(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, flip, b->policy,
+            return lbm::launch_batch_rawmrt(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy,
                                             counter, b->stream);
     }
 }
@@ -232,7 +235,7 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
     long long maxtiles = 0;
     for (int lbx : kShapes) {
         long long n = 0;
-        for (lbm_s* h : b->doms) n += tiles_of(h, lbx);
+        for (lbm_s* h : b->doms) n += tiles_of(h, lbx, 1);  // one row per thread gives the most tiles
         maxtiles = std::max(maxtiles, n);
     }
     if (maxtiles > 0x7fffffffLL / 3) {
@@ -251,7 +254,7 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) {
         b->grid = b->sms * blocks_per_sm(b->model);
-        e = upload_tiles(b, b->lbx, b->order);
+        e = upload_tiles(b, b->lbx, b->rows, b->order);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -343,12 +346,14 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e == cudaSuccess) e = refresh_domains(b);
     float best = 1e30f;
-    int best_lbx = b->lbx, best_policy = b->policy, best_order = b->order;
-    for (int lbx : kShapes) {
+    int best_lbx = b->lbx, best_rows = b->rows, best_policy = b->policy, best_order = b->order;
+    for (int rows : kRows) {
+      for (int lbx : kShapes) {
         for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
-            e = upload_tiles(b, lbx, order);
+            e = upload_tiles(b, lbx, rows, order);
             for (int policy = 0; policy < 3 && e == cudaSuccess; ++policy) {
                 b->lbx = lbx;
+                b->rows = rows;
                 b->order = order;
                 b->policy = policy;
                 for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_single(b, k & 1);
@@ -361,18 +366,21 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
                 if (e == cudaSuccess && ms < best) {
                     best = ms;
                     best_lbx = lbx;
+                    best_rows = rows;
                     best_policy = policy;
                     best_order = order;
                 }
                 if (e == cudaSuccess) e = copy_all(false);  // back to the snapshot for the next candidate
             }
         }
+      }
     }
     b->lbx = best_lbx;
+    b->rows = best_rows;
     b->policy = best_policy;
     b->order = best_order;
     b->tuned_ms = best / trial_steps;
-    if (e == cudaSuccess) e = upload_tiles(b, b->lbx, b->order);
+    if (e == cudaSuccess) e = upload_tiles(b, b->lbx, b->rows, b->order);
     if (e == cudaSuccess) e = copy_all(false);
     cudaFreeAsync(backup, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -390,7 +398,7 @@ int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream) {
     if (!b) return fail(LBM_EINVAL, "null batch");
     if (cfg) {
         cfg[0] = 1 << b->lbx;
-        cfg[1] = lbm::kBatchThreads >> b->lbx;
+        cfg[1] = (lbm::kBatchThreads >> b->lbx) * b->rows;
         cfg[2] = b->policy;
         cfg[3] = b->order;
         cfg[4] = b->grid;

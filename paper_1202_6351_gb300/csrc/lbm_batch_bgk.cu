@@ -2,9 +2,9 @@
 #include "lbm_batch_impl.cuh"
 
 namespace lbm {
-cudaError_t launch_batch_bgk(int grid, const BatchDomain* doms, const int* tiles, int ntiles, int lbx, int flip,
+cudaError_t launch_batch_bgk(int grid, const BatchDomain* doms, const int* tiles, int ntiles, int lbx, int rows, int flip,
                             int policy, int* counter, cudaStream_t s) {
-    batch_kernel<LBM_BGK><<<grid, kBatchThreads, 0, s>>>(doms, tiles, ntiles, lbx, flip, policy, counter);
+    batch_kernel<LBM_BGK><<<grid, kBatchThreads, 0, s>>>(doms, tiles, ntiles, lbx, rows, flip, policy, counter);
     return cudaGetLastError();
 }
 int batch_blocks_per_sm_bgk() {

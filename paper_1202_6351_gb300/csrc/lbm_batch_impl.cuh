@@ -45,11 +45,13 @@ __device__ __forceinline__ void batch_node(const BatchDomain& D, int x, int y) {
     }
 }
 
-// tiles: 3 ints per tile (domain, tile x, tile y); bx = 1 << lbx threads along x.
+// tiles: 3 ints per tile (domain, tile x, tile y); bx = 1 << lbx threads along x;
+// a tile is bx x (by rows) nodes and each thread updates `rows` of its rows
+// (node rows ly, ly + by, ...), which spreads the tile's decode over more nodes.
 template <int MODEL>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchDomain* __restrict__ doms,
                                                               const int* __restrict__ tiles, int ntiles, int lbx,
-                                                              int flip, int policy, int* counter) {
+                                                              int rows, int flip, int policy, int* counter) {
     __shared__ int s_next;
     const int bx = 1 << lbx, by = kBatchThreads >> lbx;
     const int lx = threadIdx.x & (bx - 1), ly = threadIdx.x >> lbx;
@@ -73,10 +75,15 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchDomain*
         if (t >= end) break;
         const int dom = tiles[3 * t];
         const BatchDomain& D = doms[dom];
-        const int x = tiles[3 * t + 1] * bx + lx, y = tiles[3 * t + 2] * by + ly;
-        if (x < D.a.nx && y < D.a.ny) {
-            if ((D.parity ^ flip) & 1) batch_node<MODEL, true>(D, x, y);
-            else batch_node<MODEL, false>(D, x, y);
+        const int x = tiles[3 * t + 1] * bx + lx, y0 = tiles[3 * t + 2] * by * rows + ly;
+        const bool odd = ((D.parity ^ flip) & 1) != 0;
+        if (x < D.a.nx) {
+            for (int r = 0; r < rows; ++r) {
+                const int y = y0 + r * by;
+                if (y >= D.a.ny) break;
+                if (odd) batch_node<MODEL, true>(D, x, y);
+                else batch_node<MODEL, false>(D, x, y);
+            }
         }
         if (policy != kPolicyDynamic) t += stride;
     }
