@@ -7,7 +7,9 @@
 // u from Eq. (26)-(27).  Reverse: lambda^T = dL/df^T; for n = T-1 .. 0
 //   mu_a(x) = lambda^{n+1}_a(x + e_a)             (transpose of the pull: a push)
 //   lambda^n(x) = (dC/df)^T mu(x)                  (collide_cascaded_vjp, in registers)
-//   dL/dF(x) += (dC/dF)^T mu(x)  (FP64 per node),   dL/dc += (dC/dc)^T mu(x)  (FP64 sums)
+//   dL/dF(x) += (dC/dF)^T mu(x),                   dL/dc += (dC/dc)^T mu(x)  (FP64 sums)
+// with dL/dF summed in the arithmetic type over the steps of one checkpoint
+// segment and in FP64 across segments (and over the whole run for FP64 storage)
 // and finally dL/du0 = (df^0/du0)^T lambda^0.  The states f^n are recomputed one
 // segment at a time from checkpoints taken every `every` steps.
 #include <algorithm>
@@ -88,10 +90,15 @@ __global__ void __launch_bounds__(kThreads) adj_final_kernel(const Args a, bool 
 }
 
 // One reverse step: lambda^n from lambda^{n+1} at the state f^n held in a.f.
+// The force gradient of the step goes into gs, in the arithmetic type: written
+// on the first reverse step of a checkpoint segment (`first`), added after
+// that; adj_fold_kernel adds each segment's sum into the FP64 gradient (for
+// FP64 storage gs is the FP64 gradient itself and `first` is false).
 template <int ST>
 __global__ void __launch_bounds__(kThreads) adj_step_kernel(const Args a, bool odd, int force,
                                                             const typename Store<ST>::R* __restrict__ lin,
-                                                            typename Store<ST>::R* __restrict__ lout, double* gF,
+                                                            typename Store<ST>::R* __restrict__ lout,
+                                                            typename Store<ST>::R* __restrict__ gs, bool first,
                                                             double* gc) {
     using R = typename Store<ST>::R;
     const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
@@ -117,8 +124,13 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const Args a, bool o
 #pragma unroll
         for (int q = 0; q < 9; ++q) lout[q * a.plane + r0 + x] = g.d[q];
         const int n = y * a.nx + x, p = a.nx * a.ny;
-        gF[n] += double(g.Fx);
-        gF[p + n] += double(g.Fy);
+        if (first) {
+            gs[n] = g.Fx;
+            gs[p + n] = g.Fy;
+        } else {
+            gs[n] += g.Fx;
+            gs[p + n] += g.Fy;
+        }
 #pragma unroll
         for (int k = 0; k < 6; ++k) c[k] = g.c[k];
     }
@@ -164,9 +176,19 @@ __global__ void __launch_bounds__(kThreads) adj_init_kernel(const Args a, int fo
     gF[p + n] += gFy;
 }
 
+// gF[i] += gs[i] for the 2 nx ny force-gradient entries of one segment (GB300's
+// FP64 pipe is far narrower than its FP32 one: FP64 work once per segment, not
+// once per step).
+__global__ void __launch_bounds__(kThreads) adj_fold_kernel(long long count, const float* __restrict__ gs,
+                                                            double* __restrict__ gF) {
+    const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (i < count) gF[i] += double(gs[i]);
+}
+
 template <int ST>
 cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, const double* u0, const double* target,
-                        char* ckpt, char* seg, void* lam0, void* lam1, double* gF, double* acc, double* gu0) {
+                        char* ckpt, char* seg, void* lam0, void* lam1, double* gF, float* gseg, double* acc,
+                        double* gu0) {
     using R = typename Store<ST>::R;
     const Args& a = h->a;
     cudaStream_t s = h->stream;
@@ -203,12 +225,19 @@ cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, co
             ak.f = seg + k * SB;
             if ((e = launch_step_any(ak, h->store, h->model, (n0 + k - 1) & 1, fm, false, s)) != cudaSuccess) return e;
         }
+        R* gs = ST == LBM_F64 ? reinterpret_cast<R*>(gF) : reinterpret_cast<R*>(gseg);
         for (long k = len - 1; k >= 0; --k) {
             Args ak = a;
             ak.f = seg + k * SB;
-            adj_step_kernel<ST><<<grid, kThreads, 0, s>>>(ak, (n0 + k) & 1, fm, cur, nxt, gF, acc + 1);
+            const bool first = ST != LBM_F64 && k == len - 1;
+            adj_step_kernel<ST><<<grid, kThreads, 0, s>>>(ak, (n0 + k) & 1, fm, cur, nxt, gs, first, acc + 1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             std::swap(cur, nxt);
+        }
+        if (ST != LBM_F64) {
+            const long long count = 2LL * a.nx * a.ny;
+            adj_fold_kernel<<<unsigned((count + kThreads - 1) / kThreads), kThreads, 0, s>>>(count, gseg, gF);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
     adj_init_kernel<ST><<<grid, kThreads, 0, s>>>(a, fm, rho, u0, cur, gu0, gF);
@@ -255,7 +284,8 @@ extern "C" int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* r
     void* lam1 = alloc(lam_bytes);
     double* acc = static_cast<double*>(alloc(7 * sizeof(double)));
     double* gF = grad_force ? grad_force : static_cast<double*>(alloc(2 * n * sizeof(double)));
-    if (!ckpt || !seg || !lam0 || !lam1 || !acc || !gF) {
+    float* gseg = h->store == LBM_F64 ? nullptr : static_cast<float*>(alloc(2 * n * sizeof(float)));
+    if (!ckpt || !seg || !lam0 || !lam1 || !acc || !gF || (h->store != LBM_F64 && !gseg)) {
         release();
         cudaGetLastError();
         if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
@@ -265,8 +295,10 @@ extern "C" int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* r
     cudaError_t e = cudaMemsetAsync(acc, 0, 7 * sizeof(double), s);
     if (e == cudaSuccess) {
         e = h->store == LBM_F64
-                ? run_reverse<LBM_F64>(h, nsteps, every, rho, u0, u_target, ckpt, seg, lam0, lam1, gF, acc, grad_u0)
-                : run_reverse<LBM_F32>(h, nsteps, every, rho, u0, u_target, ckpt, seg, lam0, lam1, gF, acc, grad_u0);
+                ? run_reverse<LBM_F64>(h, nsteps, every, rho, u0, u_target, ckpt, seg, lam0, lam1, gF, gseg, acc,
+                                       grad_u0)
+                : run_reverse<LBM_F32>(h, nsteps, every, rho, u0, u_target, ckpt, seg, lam0, lam1, gF, gseg, acc,
+                                       grad_u0);
     }
     double host[7] = {0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, acc, sizeof host, cudaMemcpyDeviceToHost, s);
