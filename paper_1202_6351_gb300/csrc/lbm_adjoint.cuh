@@ -67,7 +67,7 @@ template <typename R>
 LBM_HD void collide_cascaded_vjp(const R d[9], R Fx, R Fy, const Coef<R>& c, const R mu[9], CollideAdjoint<R>& out) {
     // ---------------- forward recompute (same statements as collide_cascaded)
     const Moments<R> m = moments(d, c.rho0);
-    const R inv = R(1) / m.rho;
+    const R inv = recip(m.rho);  // as the forward kernel: IEEE in FP64, rcp.approx in FP32
     const R px = m.jx + R(0.5) * Fx, py = m.jy + R(0.5) * Fy;
     const R ux = px * inv, uy = py * inv;
     const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
