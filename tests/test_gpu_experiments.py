@@ -1,10 +1,14 @@
-"""Lid-driven cavity results of Sec. IV-V reproduced on the CUDA path (context
-pins: the paper's own printed numbers, at a coarser grid than the paper's)."""
+"""Results of Sec. III-V reproduced on the CUDA path: Taylor-Green decay and
+grid convergence, and the lid-driven cavity (context pins: the paper's own
+printed numbers, at a coarser grid than the paper's)."""
+import math
+
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1202_6351_gb300 import experiments as X
-from paper_1202_6351_gb300 import lbm
+from paper_1202_6351_gb300 import lbm, workloads
 from tests import _pins as P
 
 pytestmark = pytest.mark.gpu
@@ -116,6 +120,50 @@ def test_taylor_green_strain_rate_converges_at_second_order_on_the_gpu():
     slopes = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     print("S_xx errors", errs, "slopes", slopes)
     assert all(1.9 < s < 2.15 for s in slopes)
+
+
+# Relative L2 velocity error at one decay time for 16-bit storage, as measured
+# (stated bounds with some margin): FP16 rounding stalls part of the slow viscous
+# decay, so the error grows with the number of steps (see the design notes).
+ONE_DECAY_TIME_BOUNDS = {lbm.F16DEV: {64: 5e-3, 128: 1.5e-2, 256: 0.3, 1024: 6e-2},
+                         lbm.BF16DEV: {64: 0.1, 128: 0.3, 256: 0.1, 1024: 0.7}}
+
+
+def test_taylor_green_to_one_decay_time():
+    """The Taylor-Green configuration (Sec. III-B) on N = 64, 128, 256, 1024, run
+    to one decay time T = N^2 / (8 pi^2 nu) (1245 .. 318729 steps) and checked
+    against the analytic decay: in FP32 the velocity error falls at second order
+    (the paper: slopes 1.98-1.99), and S_xx from the moments (Eq. 28-30) too up
+    to N = 256 (at 1024 FP32 rounding of the small non-equilibrium moments sets a
+    floor near 1e-5); the 16-bit stores meet their stated bounds."""
+    om = 1.6
+    nu = O.nu_from_omega(om)
+    oms = (1.0, om, om, 1.0, 1.0, 1.0)
+    sides = (64, 128, 256, 1024)
+    errs = {}
+    for st in (lbm.F32, lbm.F16DEV, lbm.BF16DEV):
+        for n in sides:
+            u0 = workloads.diffusive_u0(n)
+            T = int(round(O.taylor_green_decay_time(n, nu)))
+            rho, u = workloads.taylor_green_init(n, u0)
+            with lbm.Lattice(n, n, oms, store=st) as L:
+                L.init(rho, u).step(T)
+                r, ug = L.macros()
+                sxx = L.strain()[0] / r
+            _, ua, sa = O.taylor_green(n, u0, nu, T)
+            errs[st, n] = (float(np.sqrt(((ug - ua) ** 2).sum() / (ua ** 2).sum())),
+                           float(np.sqrt(((sxx - sa) ** 2).sum() / (sa ** 2).sum())))
+            print(lbm.STORE_NAMES[st], n, T, "u error %.3e, S_xx error %.3e" % errs[st, n])
+    for a, b in zip(sides, sides[1:]):
+        slope_u = math.log(errs[lbm.F32, a][0] / errs[lbm.F32, b][0]) / math.log(b / a)
+        assert 1.85 < slope_u < 2.2, (a, b, slope_u)
+        if b <= 256:
+            slope_s = math.log(errs[lbm.F32, a][1] / errs[lbm.F32, b][1]) / math.log(b / a)
+            assert 1.85 < slope_s < 2.2, (a, b, slope_s)
+    assert errs[lbm.F32, 1024][1] < 2e-5
+    for st, bounds in ONE_DECAY_TIME_BOUNDS.items():
+        for n, bound in bounds.items():
+            assert errs[st, n][0] <= bound, (lbm.STORE_NAMES[st], n, errs[st, n][0])
 
 
 def test_cavity_grid_convergence_second_order():
