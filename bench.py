@@ -396,8 +396,13 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
     ref.close()
     out["cascaded_f64"] = {"mlups": round(nodes * steps / s64 / 1e6, 1),
                            "frac": round(lbm.lbm_bytes_per_update(lbm.F64) * nodes * steps / s64 / 1e9 / peak, 4)}
-    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV), ("bf16", lbm.BF16DEV)):
+    runs = (("f32", lbm.F32, lbm.ROUND_NEAREST), ("f16", lbm.F16DEV, lbm.ROUND_NEAREST),
+            ("bf16", lbm.BF16DEV, lbm.ROUND_NEAREST), ("f16_stochastic", lbm.F16DEV, lbm.ROUND_STOCHASTIC),
+            ("bf16_stochastic", lbm.BF16DEV, lbm.ROUND_STOCHASTIC))
+    for name, st, rounding in runs:
         L = make(lbm.CASCADED, st)
+        if rounding == lbm.ROUND_STOCHASTIC:
+            L.set_rounding(rounding, 2026)
         L.step(10)
         s, _, _ = timed(L, steps)
         _, u = L.macros()

@@ -60,8 +60,8 @@ extern "C" {
  * The stored quantity is the deviation f_a - w_a rho0 (w = 4/9, 1/9, 1/36). */
 #define LBM_F64 0
 #define LBM_F32 1
-#define LBM_BF16DEV 2 /* bfloat16, round to nearest even */
-#define LBM_F16DEV 3  /* IEEE half of 4096 * deviation, round to nearest even */
+#define LBM_BF16DEV 2 /* bfloat16, round to nearest even (or stochastically: lbm_set_rounding) */
+#define LBM_F16DEV 3  /* IEEE half of 4096 * deviation, rounded as LBM_BF16DEV */
 
 /* boundary specification: edge[k] is the kind of edge k (W, E, S, N);
  * wall_u[k] the tangential speed of a moving wall (along x on the south and
@@ -120,6 +120,23 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
  * variant outside 0..2. */
 int lbm_set_variant(lbm_t h, int variant);
+
+/* Rounding of the stored 16-bit deviations (LBM_BF16DEV, LBM_F16DEV).
+ * LBM_ROUND_NEAREST (the default) rounds to nearest even.  LBM_ROUND_STOCHASTIC
+ * rounds each stored value up with probability equal to its distance above the
+ * representable value below, in units of their spacing, so that the stored
+ * state is an unbiased estimate of the computed one.  Round to nearest loses
+ * every per-step change smaller than half a spacing; over long runs this stalls
+ * the slow viscous decay (a Taylor-Green vortex on 256^2 in FP16 ends one decay
+ * time 22 % too strong), which stochastic rounding removes.  The random bits
+ * come from a counter-based hash of (seed, step, node, population): a run is
+ * reproducible for a given seed, independent of kernel variant, CTA shape and
+ * CUDA-graph replay.  Costs extra integer instructions per stored value.
+ * LBM_EINVAL for another mode or for stochastic rounding with FP32/FP64
+ * storage.  Lattices with stochastic rounding cannot be batched. */
+#define LBM_ROUND_NEAREST 0
+#define LBM_ROUND_STOCHASTIC 1
+int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
  * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads) on

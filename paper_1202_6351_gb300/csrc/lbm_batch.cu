@@ -224,6 +224,7 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
         if (h->store != LBM_F32 && h->store != LBM_F16DEV && h->store != LBM_BF16DEV)
             return fail(LBM_EINVAL, "lbm_batch_create: storage must be LBM_F32, LBM_BF16DEV or LBM_F16DEV");
         if (h->has_field) return fail(LBM_EINVAL, "lbm_batch_create: per-node force fields are not batched");
+        if (h->a.rseed) return fail(LBM_EINVAL, "lbm_batch_create: stochastic rounding is not batched");
         for (int j = 0; j < i; ++j)
             if (lattices[j] == h) return fail(LBM_EINVAL, "lbm_batch_create: a lattice appears twice");
     }
@@ -297,6 +298,9 @@ int lbm_batch_step(lbm_batch_t b, long n) {
     if (n < 0) return fail(LBM_EINVAL, "lbm_batch_step: n must be >= 0");
     if (n == 0) return LBM_OK;
     Guard g(b->device);
+    for (lbm_s* h : b->doms)
+        if (h->a.rseed || h->has_field)
+            return fail(LBM_EINVAL, "lbm_batch_step: a lattice now has stochastic rounding or a force field");
     BATCH_CUDA(wait_for_domains(b), "lbm_batch_step: waiting for the lattices' streams");
     BATCH_CUDA(refresh_domains(b), "lbm_batch_step: domain table");
     long done = 0;

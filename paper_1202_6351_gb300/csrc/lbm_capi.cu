@@ -96,7 +96,18 @@ size_t elem_size(int store) {
 using lbm::force_mode;
 
 cudaError_t launch_step(lbm_s* h, bool odd) {
+    if (h->a.rseed) {  // stochastic rounding: the hash of (seed, step) of this launch
+        h->a.rbase = lbm::round_hash(h->a.rseed, static_cast<unsigned long long>(h->t));
+        h->a.rtable = nullptr;
+        h->a.tstep = 0;
+    }
     return lbm::launch_step_any(h->a, h->store, h->model, odd, force_mode(h), h->walls, h->stream);
+}
+
+// rtable[k] = the hash of (seed, t0 + k) for the k-th launch of a graph replay.
+__global__ void fill_round_table(unsigned* rtable, unsigned long long seed, unsigned long long t0, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) rtable[k] = lbm::round_hash(seed, t0 + static_cast<unsigned long long>(k));
 }
 
 long long nodes(const lbm_s* h) { return (long long)h->a.nx * h->a.ny; }
@@ -114,6 +125,7 @@ struct DevBuf {
 bool same_launch(const Args& x, const Args& y) {
     if (x.f != y.f || x.plane != y.plane || x.nx != y.nx || x.ny != y.ny || x.pitch != y.pitch) return false;
     if (x.ffield != y.ffield || x.variant != y.variant || x.block_x != y.block_x || x.scale != y.scale) return false;
+    if (x.rseed != y.rseed) return false;
     for (int k = 0; k < 4; ++k)
         if (x.wall[k] != y.wall[k] || x.wallx[k] != y.wallx[k] || x.wally[k] != y.wally[k] ||
             x.wallxf[k] != y.wallxf[k] || x.wallyf[k] != y.wallyf[k])
@@ -136,11 +148,25 @@ cudaError_t capture_graph(lbm_s* h, int fm) {
     if (e == cudaSuccess && !h->ev_in) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess && !h->ev_out) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
+    if (h->a.rseed && h->rtable_cap < h->graph_steps) {  // one hash per launch of a replay
+        if (h->d_rtable) cudaFree(h->d_rtable);             // (synchronous: no replay still reads it)
+        h->d_rtable = nullptr;
+        h->rtable_cap = 0;
+        e = cudaMalloc((void**)&h->d_rtable, h->graph_steps * sizeof(unsigned));
+        if (e != cudaSuccess) return e;
+        h->rtable_cap = h->graph_steps;
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k)
-        e = lbm::launch_step_any(h->a, h->store, h->model, (k & 1) != 0, fm, h->walls, h->gstream);
+    for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k) {
+        lbm::Args ak = h->a;
+        if (ak.rseed) {
+            ak.rtable = h->d_rtable;
+            ak.tstep = k;
+        }
+        e = lbm::launch_step_any(ak, h->store, h->model, (k & 1) != 0, fm, h->walls, h->gstream);
+    }
     cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -160,6 +186,11 @@ cudaError_t replay_graph(lbm_s* h) {
     if (!h->graph || fm != h->graph_force || !same_launch(h->a, h->graph_args)) e = capture_graph(h, fm);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_in, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gstream, h->ev_in, 0);
+    if (e == cudaSuccess && h->a.rseed) {
+        fill_round_table<<<(h->graph_steps + 255) / 256, 256, 0, h->gstream>>>(
+            h->d_rtable, h->a.rseed, static_cast<unsigned long long>(h->t), h->graph_steps);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaGraphLaunch(h->graph, h->gstream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_out, h->gstream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_out, 0);
@@ -298,6 +329,7 @@ int lbm_destroy(lbm_t h) {
         if (h->state) cudaFree(h->state);
         if (h->ffield) cudaFree(h->ffield);
         if (h->partials) cudaFree(h->partials);
+        if (h->d_rtable) cudaFree(h->d_rtable);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "lbm_destroy");
     }
@@ -338,6 +370,20 @@ int lbm_set_graph_steps(lbm_t h, int steps) {
     if (h->gstream) LBM_CUDA(cudaStreamSynchronize(h->gstream), "graph stream sync");
     drop_graph(h);
     h->graph_steps = steps;
+    return LBM_OK;
+}
+
+int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed) {
+    CHECK_HANDLE(h);
+    if (mode != LBM_ROUND_NEAREST && mode != LBM_ROUND_STOCHASTIC)
+        return fail(LBM_EINVAL, "rounding mode must be LBM_ROUND_NEAREST or LBM_ROUND_STOCHASTIC");
+    if (mode == LBM_ROUND_STOCHASTIC && h->store != LBM_F16DEV && h->store != LBM_BF16DEV)
+        return fail(LBM_EINVAL, "stochastic rounding applies to LBM_BF16DEV and LBM_F16DEV storage");
+    // rseed != 0 selects stochastic rounding; mix the caller's seed into a nonzero word
+    h->a.rseed = mode == LBM_ROUND_STOCHASTIC ? ((seed ^ 0x2545f4914f6cdd1dULL) | 1ULL) : 0ULL;
+    h->a.rtable = nullptr;
+    h->a.rbase = 0;
+    h->a.tstep = 0;
     return LBM_OK;
 }
 

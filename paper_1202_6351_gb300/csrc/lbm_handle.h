@@ -31,4 +31,8 @@ struct lbm_s {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     lbm::Args graph_args{};
     int graph_force = -1;
+    // Stochastic rounding of 16-bit stores (lbm_set_rounding): per-step hashes
+    // C0 of a graph replay, filled on the graph stream before each replay.
+    unsigned* d_rtable = nullptr;
+    int rtable_cap = 0;
 };

@@ -16,12 +16,12 @@
 
 namespace lbm {
 
-template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false>
 __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
+    step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y);
 }
 
 // Two rows per thread (nodes (x, y) and (x, y + 1)) with packed FP32x2
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, 4) step_kernel_pair(const A
 // Register budget per parity, as measured: the even step keeps all nine planes
 // aligned and spills at 64 registers, so it gets 80 (3 CTAs per SM); the odd
 // step runs faster with more warps at 64 (4 CTAs per SM).
-template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR>
 __global__ void __launch_bounds__(kStepBX * kStepBY, ODD ? 4 : 3) step_kernel_vec(const Args a) {
     const int x0 = N * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -57,10 +57,10 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, ODD ? 4 : 3) step_kernel_ve
                                     : (x0 + N <= a.nx));
     const unsigned vmask = ODD ? __ballot_sync(0xffffffffu, vec) : 0u;
     if (vec) {
-        step_vec<N, MODEL, STORE, ODD, FORCE>(a, x0, y, vmask, threadIdx.x & 31);
+        step_vec<N, MODEL, STORE, ODD, FORCE, SR>(a, x0, y, vmask, threadIdx.x & 31);
     } else if (inside) {
         const int x1 = min(x0 + N, a.nx);
-        for (int x = x0; x < x1; ++x) step_node_split<MODEL, STORE, ODD, FORCE, WALLS>(a, x, y);
+        for (int x = x0; x < x1; ++x) step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y);
     }
 }
 
@@ -72,19 +72,30 @@ static inline dim3 fit_block(int bx, int width) {
     return dim3(bx, (kStepBX * kStepBY) / bx);
 }
 
-template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
+template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR>
 static cudaError_t launch_vec(const Args& a, cudaStream_t s) {
     const int vecs = (a.nx + N - 1) / N;
     const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, vecs);
     const dim3 grid((vecs + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
-    step_kernel_vec<N, MODEL, STORE, ODD, FORCE, WALLS><<<grid, block, 0, s>>>(a);
+    step_kernel_vec<N, MODEL, STORE, ODD, FORCE, WALLS, SR><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
-    if constexpr ((STORE == LBM_F16DEV || STORE == LBM_BF16DEV) && FORCE != 2) {
-        if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS>(a, s);
+    if constexpr (STORE == LBM_F16DEV || STORE == LBM_BF16DEV) {
+        if (a.rseed) {  // stochastic rounding: variants 0 and 2 (variant 1 runs variant 0)
+            if constexpr (FORCE != 2) {
+                if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, true>(a, s);
+            }
+            const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
+            const dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
+            step_kernel<MODEL, STORE, ODD, FORCE, WALLS, true><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        if constexpr (FORCE != 2) {
+            if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, false>(a, s);
+        }
     }
     const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
     const int bx = block.x, by = block.y;

@@ -100,7 +100,7 @@ __device__ __forceinline__ void store_words(unsigned short* p, const uint32_t* w
 // neighbour (warp shuffles), so that each lane loads and stores exactly its
 // own aligned vector; a lane whose neighbour is outside `vmask` (warp or row
 // edge) loads that element and stores its shifted range with narrow stores.
-template <int N, int MODEL, int STORE, bool ODD, int FORCE>
+template <int N, int MODEL, int STORE, bool ODD, int FORCE, bool SR = false>
 __device__ __forceinline__ void step_vec(const Args& a, int x0, int y, unsigned vmask, int lane) {
     using H = Half16<STORE>;
     constexpr int W = N / 2;  // words per vector
@@ -145,9 +145,13 @@ __device__ __forceinline__ void step_vec(const Args& a, int x0, int y, unsigned 
     // halves exist.
     //   s = 0:   words (0,1) (2,3) ...                       -> ow[p][0 .. W-1]
     //   s = +-1: single 0, words (1,2) (3,4) ..., single N-1 -> os0, ow[p][0 .. W-2], os1
+    // With stochastic rounding (SR) every value is encoded as soon as it exists,
+    // from the offset of its own node and direction (as in store_node).
     float prev[9];
+    unsigned short prevh[9];
     uint32_t ow[9][W];
     unsigned short os0[9], os1[9];
+    const unsigned rbase = SR ? round_base(a) : 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         float d[9];
@@ -162,18 +166,32 @@ __device__ __forceinline__ void step_vec(const Args& a, int x0, int y, unsigned 
             d[q] = v;
         }
         collide<MODEL, float, (FORCE != 0)>(d, Fx, Fy, c);
+        const unsigned rn = SR ? round_node(a, rbase, x0 + i, y) : 0u;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int p = ODD ? q : opp(q);  // plane receiving node i's output for direction q
             const int s = ODD ? cx(p) : 0;
-            if (s == 0) {
-                if (i & 1) ow[p][i >> 1] = H::pack(prev[p], d[q]);
+            if constexpr (SR) {
+                const unsigned short hv = StochasticRound<STORE>::enc(d[q], rn + static_cast<unsigned>(q) * kRoundStride);
+                const uint32_t pair = static_cast<uint32_t>(prevh[p]) | (static_cast<uint32_t>(hv) << 16);
+                if (s == 0) {
+                    if (i & 1) ow[p][i >> 1] = pair;
+                } else {
+                    if (i == 0) os0[p] = hv;
+                    else if (i == N - 1) os1[p] = hv;
+                    else if (!(i & 1)) ow[p][(i >> 1) - 1] = pair;
+                }
+                prevh[p] = hv;
             } else {
-                if (i == 0) os0[p] = H::enc(d[q]);
-                else if (i == N - 1) os1[p] = H::enc(d[q]);
-                else if (!(i & 1)) ow[p][(i >> 1) - 1] = H::pack(prev[p], d[q]);
+                if (s == 0) {
+                    if (i & 1) ow[p][i >> 1] = H::pack(prev[p], d[q]);
+                } else {
+                    if (i == 0) os0[p] = H::enc(d[q]);
+                    else if (i == N - 1) os1[p] = H::enc(d[q]);
+                    else if (!(i & 1)) ow[p][(i >> 1) - 1] = H::pack(prev[p], d[q]);
+                }
+                prev[p] = d[q];
             }
-            prev[p] = d[q];
         }
     }
 

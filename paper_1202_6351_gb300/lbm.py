@@ -20,6 +20,7 @@ PERIODIC, BOUNCEBACK, MOVING_WALL = 0, 1, 2
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 CASCADED, BGK, RAWMRT = 0, 1, 2
 F64, F32, BF16DEV, F16DEV = 0, 1, 2, 3
+ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
 STORE_NAMES = {F64: "f64", F32: "f32", BF16DEV: "bf16", F16DEV: "f16"}
 MODEL_NAMES = {CASCADED: "cascaded", BGK: "bgk", RAWMRT: "rawmrt"}
 
@@ -53,6 +54,7 @@ SIGNATURES = {
     "lbm_set_omegas": (_i, [_vp, _dp]),
     "lbm_set_graph_steps": (_i, [_vp, _i]),
     "lbm_set_variant": (_i, [_vp, _i]),
+    "lbm_set_rounding": (_i, [_vp, _i, C.c_ulonglong]),
     "lbm_tune": (_i, [_vp, _i, C.POINTER(C.c_float)]),
     "lbm_set_force_field": (_i, [_vp, _vp, _i]),
     "lbm_init": (_i, [_vp, _vp, _vp]),
@@ -245,6 +247,11 @@ class Lattice:
 
     def set_variant(self, variant):
         _check(self.lib.lbm_set_variant(self.h, int(variant)))
+        return self
+
+    def set_rounding(self, mode, seed=0):
+        """ROUND_NEAREST or ROUND_STOCHASTIC (16-bit storage) with a seed."""
+        _check(self.lib.lbm_set_rounding(self.h, int(mode), int(seed) & (2 ** 64 - 1)))
         return self
 
     def tune(self, trial_steps=20):

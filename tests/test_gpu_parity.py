@@ -449,6 +449,68 @@ def test_init_and_macros_read_and_write_pinned_host_buffers_in_place(store):
     np.testing.assert_array_equal(results[1][2], results[1][3])
 
 
+# ---------------------------------------------------------------- stochastic rounding of 16-bit stores
+
+@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV], ids=["f16", "bf16"])
+@pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
+@pytest.mark.parametrize("edges,force", [("periodic", (0.0, 0.0)), ("cavity", (0.0, 0.0)),
+                                         ("channel", (2e-5, 1e-5))])
+def test_stochastic_rounding_is_the_same_in_every_variant_and_graph_length(store, model, edges, force):
+    """The random bits depend only on (seed, step, node, population): the
+    four-node kernel, the one-node kernel and CUDA-graph replays of any length
+    give the same states bit for bit; the same seed repeats a run, another seed
+    does not."""
+    nx, ny = 70, 37
+    e, wu = EDGES[edges]
+    rho, u = workloads.random_fields(41, nx, ny, u_amp=0.03, rho_amp=0.01)
+
+    def run(variant, graph_steps, seed):
+        g = lbm.Lattice(nx, ny, OMEGAS, force=force, edges=e, wall_u=wu, model=model, store=store)
+        g.set_variant(variant).set_graph_steps(graph_steps).set_rounding(lbm.ROUND_STOCHASTIC, seed)
+        g.init(rho, u)
+        out = []
+        for n in (3, 8, 21):
+            g.step(n)
+            out.append(g.get_f())
+        g.close()
+        return out
+
+    ref = run(0, 0, 7)
+    for variant, graph_steps in ((2, 0), (0, 8), (2, 8), (2, 64)):
+        for k, (a, b) in enumerate(zip(run(variant, graph_steps, 7), ref)):
+            np.testing.assert_array_equal(a, b, err_msg=f"variant {variant}, graph {graph_steps}, chunk {k}")
+    other = run(0, 0, 8)
+    assert not np.array_equal(other[-1], ref[-1])
+    nearest = lbm.Lattice(nx, ny, OMEGAS, force=force, edges=e, wall_u=wu, model=model, store=store)
+    nearest.init(rho, u).step(32)
+    f_rn = nearest.get_f()
+    nearest.close()
+    assert not np.array_equal(f_rn, ref[-1])
+    assert np.abs(ref[-1] - f_rn).max() <= 1e-3  # the same flow, rounded differently
+
+
+@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV], ids=["f16", "bf16"])
+def test_stochastic_rounding_keeps_mass_and_rejects_misuse(store):
+    n = 128
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    g = lbm.Lattice(n, n, OMEGAS, store=store).set_rounding(lbm.ROUND_STOCHASTIC, 3).init(rho, u)
+    m0 = g.stats()[0]
+    g.step(1000)
+    m1 = g.stats()[0]
+    assert abs(m1 - m0) / m0 <= (2e-6 if store == lbm.F16DEV else 2e-5)
+    with pytest.raises(lbm.LBMError):
+        g.set_rounding(5)
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([g])
+    g.set_rounding(lbm.ROUND_NEAREST)
+    g.close()
+    f32 = lbm.Lattice(16, 16, OMEGAS, store=lbm.F32)
+    with pytest.raises(lbm.LBMError):
+        f32.set_rounding(lbm.ROUND_STOCHASTIC, 1)
+    f32.set_rounding(lbm.ROUND_NEAREST)
+    f32.close()
+
+
 def test_tune_keeps_state_and_picks_a_variant():
     n = 256
     rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
