@@ -19,10 +19,11 @@
  *     sits at x = i, y = j; half-way bounce-back walls sit half a link outside
  *     the first and last nodes.
  *   - "host" pointers are ordinary (pageable or pinned) CPU memory; the call
- *     copies through a stream-ordered device buffer and returns after the copy
- *     has completed.  "device" pointers are CUDA device memory of the device
- *     that was current at lbm_create; those calls are asynchronous on the
- *     handle's stream.
+ *     copies through a stream-ordered device buffer (lbm_init and lbm_macros
+ *     access mapped page-locked buffers in place instead) and returns after
+ *     the transfer has completed.  "device" pointers are CUDA device memory of
+ *     the device that was current at lbm_create; those calls are asynchronous
+ *     on the handle's stream.
  *   - A handle is used by one host thread at a time.  The library owns the
  *     device memory it allocates; lbm_destroy releases it.
  */
@@ -45,7 +46,9 @@ extern "C" {
 /* edge kinds, one per edge in the order west, east, south, north */
 #define LBM_PERIODIC 0
 #define LBM_BOUNCEBACK 1   /* half-way bounce-back, wall at rest (Sec. III-A) */
-#define LBM_MOVING_WALL 2  /* half-way bounce-back with the moving-wall correction (Sec. III-C) */
+#define LBM_MOVING_WALL 2  /* half-way bounce-back with the moving-wall correction (Sec. III-C);
+                              a diagonal link through a corner where two walls meet is bounced
+                              back without it */
 #define LBM_WEST 0
 #define LBM_EAST 1
 #define LBM_SOUTH 2
@@ -60,8 +63,8 @@ extern "C" {
  * The stored quantity is the deviation f_a - w_a rho0 (w = 4/9, 1/9, 1/36). */
 #define LBM_F64 0
 #define LBM_F32 1
-#define LBM_BF16DEV 2 /* bfloat16, round to nearest even (or stochastically: lbm_set_rounding) */
-#define LBM_F16DEV 3  /* IEEE half of 4096 * deviation, rounded as LBM_BF16DEV */
+#define LBM_BF16DEV 2 /* bfloat16 deviation, round to nearest even (or stochastically: lbm_set_rounding) */
+#define LBM_F16DEV 3  /* IEEE half of 4096 x deviation, rounded as LBM_BF16DEV */
 
 /* boundary specification: edge[k] is the kind of edge k (W, E, S, N);
  * wall_u[k] the tangential speed of a moving wall (along x on the south and
@@ -131,7 +134,8 @@ int lbm_set_variant(lbm_t h, int variant);
  * time 22 % too strong), which stochastic rounding removes.  The random bits
  * come from a counter-based hash of (seed, step, node, population): a run is
  * reproducible for a given seed, independent of kernel variant, CTA shape and
- * CUDA-graph replay.  Costs extra integer instructions per stored value.
+ * CUDA-graph replay (variant 1 runs variant 0 in this mode).  Costs extra
+ * integer instructions per stored value.
  * LBM_EINVAL for another mode or for stochastic rounding with FP32/FP64
  * storage.  Lattices with stochastic rounding cannot be batched. */
 #define LBM_ROUND_NEAREST 0
@@ -169,7 +173,7 @@ int lbm_init_device(lbm_t h, const double* rho, const double* u);
  * of at least lbm_set_graph_steps steps starting at an even step are replayed
  * from a CUDA graph on an internal stream that is ordered after the handle's
  * stream and before any later work on it (the graph is recaptured whenever a
- * rate, force, force field or variant has changed).  With the divergence
+ * rate, force, force field, variant or rounding mode has changed).  With the divergence
  * check on (lbm_set_check) no graph is used, the call synchronises at every
  * check and returns LBM_EDIVERGED when it fails. */
 int lbm_step(lbm_t h, long n);
@@ -249,7 +253,8 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
  * per-node update is exactly that of lbm_step, so results are bitwise equal.
  * Chunks of `graph_steps` steps (default 100, even) are replayed from a CUDA
  * graph.  All lattices must share the device and the collision model, use
- * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage and have no per-node force field;
+ * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage with round-to-nearest and have no
+ * per-node force field;
  * storage kinds, sizes, edges and uniform forces may differ.  The batch works
  * on its own stream: lbm_batch_step first waits (on the host) for the
  * lattices' streams, and later work on those streams waits for the batch.
@@ -259,7 +264,9 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
 typedef struct lbm_batch_s* lbm_batch_t;
 
 /* Errors: LBM_EINVAL (count < 1, NULL or repeated lattice, mixed devices or
- * models, FP64 storage, a force field), LBM_ENOMEM, LBM_ECUDA. */
+ * models, FP64 storage, a force field, stochastic rounding), LBM_ENOMEM,
+ * LBM_ECUDA.  lbm_batch_step fails with LBM_EINVAL if a lattice has since been
+ * given a force field or stochastic rounding. */
 int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out);
 int lbm_batch_destroy(lbm_batch_t b);
 
