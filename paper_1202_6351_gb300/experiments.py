@@ -3,7 +3,7 @@
 * :func:`cavity_steady` runs a lid-driven cavity to steady state (max |du| over
   1000 steps below a tolerance) and returns its velocity field.
 * :func:`vortex_centre` locates the primary vortex (Sec. IV-C, Table I) from
-  the stream function psi(x, y) = sum of u along y from the bottom wall.
+  the stream function psi(x, y), the integral of u along y from the bottom wall.
 * :func:`max_stable_cell_reynolds` finds, for one collision model and grid,
   the largest cell Reynolds number Re_c = U dx / nu at which the cavity stays
   stable (Sec. V, Table IV), running many viscosities side by side in one
@@ -81,8 +81,10 @@ def strain_at_points(rho, u, strain):
 
 
 def stream_function(u):
-    """psi[j, i] = sum_{k <= j} u_x[k, i] (unit spacing; psi = 0 below the bottom wall)."""
-    return np.cumsum(u[0], axis=0)
+    """psi[j, i] = sum_{k < j} u_x[k, i] + u_x[j, i] / 2: the integral of u_x from
+    the bottom wall (psi = 0 there, half a spacing below node row 0) up to the
+    node itself, cell by cell with the midpoint rule (unit spacing)."""
+    return np.cumsum(u[0], axis=0) - 0.5 * u[0]
 
 
 def _parabola_vertex(fm, f0, fp):
