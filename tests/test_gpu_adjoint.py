@@ -189,6 +189,26 @@ def test_adjoint_512_f32_agrees_with_f64(adjoint_512):
     assert np.sqrt(((gf32 - gf64) ** 2).sum() / (gf64 ** 2).sum()) <= 1e-4
 
 
+@pytest.mark.parametrize("every", [1, 7, 40, 100])
+def test_f32_force_gradient_folding_for_any_checkpoint_interval(every):
+    """FP32 storage sums the force gradient in FP32 within a checkpoint segment
+    and folds it into FP64 once per segment: one step per segment, a ragged
+    last segment (40 = 5 x 7 + 5) and a single segment longer than the run must
+    all give the FP64 adjoint's gradients to FP32 accuracy."""
+    n, steps = 32, 40
+    om = (1.0, 1.6, 1.6, 1.0, 1.0, 1.0)
+    rng = np.random.default_rng(11)
+    u0 = 0.02 * rng.standard_normal((2, n, n))
+    F = 1e-5 * rng.standard_normal((2, n, n))
+    target = 0.02 * rng.standard_normal((2, n, n))
+    ref = gpu_adjoint(n, n, om, u0, F, target, steps, 7, store=lbm.F64)
+    got = gpu_adjoint(n, n, om, u0, F, target, steps, every, store=lbm.F32)
+    assert got[0] == pytest.approx(ref[0], rel=1e-5)
+    for a, b in zip(got[1:3], ref[1:3]):
+        assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max()
+    np.testing.assert_allclose(got[3], ref[3], rtol=1e-3, atol=1e-6 * np.abs(ref[3]).max())
+
+
 def test_autograd_function_returns_the_adjoint_gradients():
     import torch
 
