@@ -137,7 +137,8 @@ int lbm_set_variant(lbm_t h, int variant);
  * CUDA-graph replay (variant 1 runs variant 0 in this mode).  Costs extra
  * integer instructions per stored value.
  * LBM_EINVAL for another mode or for stochastic rounding with FP32/FP64
- * storage.  Lattices with stochastic rounding cannot be batched. */
+ * storage.  Batches (lbm_batch_*) round each lattice as it is set here, with
+ * the same results as lbm_step. */
 #define LBM_ROUND_NEAREST 0
 #define LBM_ROUND_STOCHASTIC 1
 int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
@@ -253,8 +254,7 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
  * per-node update is exactly that of lbm_step, so results are bitwise equal.
  * Chunks of `graph_steps` steps (default 100, even) are replayed from a CUDA
  * graph.  All lattices must share the device and the collision model, use
- * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage with round-to-nearest and have no
- * per-node force field;
+ * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage and have no per-node force field;
  * storage kinds, sizes, edges and uniform forces may differ.  The batch works
  * on its own stream: lbm_batch_step first waits (on the host) for the
  * lattices' streams, and later work on those streams waits for the batch.
@@ -264,9 +264,8 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
 typedef struct lbm_batch_s* lbm_batch_t;
 
 /* Errors: LBM_EINVAL (count < 1, NULL or repeated lattice, mixed devices or
- * models, FP64 storage, a force field, stochastic rounding), LBM_ENOMEM,
- * LBM_ECUDA.  lbm_batch_step fails with LBM_EINVAL if a lattice has since been
- * given a force field or stochastic rounding. */
+ * models, FP64 storage, a force field), LBM_ENOMEM, LBM_ECUDA.  lbm_batch_step
+ * fails with LBM_EINVAL if a lattice has since been given a force field. */
 int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out);
 int lbm_batch_destroy(lbm_batch_t b);
 

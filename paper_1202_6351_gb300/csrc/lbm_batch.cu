@@ -11,9 +11,26 @@
 #include "lbm_handle.h"
 
 namespace lbm {
-cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
-cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
-cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int, int*, cudaStream_t);
+cudaError_t launch_batch_cascaded(int, const BatchDomain*, const int*, int, int, int, int, int, int*, const unsigned*, int,
+                                  int, cudaStream_t);
+cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int, int, int, int*, const unsigned*, int, int,
+                             cudaStream_t);
+cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int, int*, const unsigned*, int,
+                                int, cudaStream_t);
+
+// rtab[d * rstride + k] = the hash of (seed, t + base + k) of domain d, for the
+// k-th launch of a sequence that starts `base` steps after the domains' counts t.
+__global__ void __launch_bounds__(kBatchThreads) fill_batch_round_table(const BatchDomain* __restrict__ doms,
+                                                                        int ndoms, unsigned* rtab, int rstride,
+                                                                        long long base) {
+    const int i = blockIdx.x * kBatchThreads + threadIdx.x;
+    if (i >= ndoms * rstride) return;
+    const int d = i / rstride, k = i % rstride;
+    const BatchDomain& D = doms[d];
+    rtab[i] = D.a.rseed ? round_hash(D.a.rseed, static_cast<unsigned long long>(D.t + base + k)) : 0u;
+}
+
+
 int batch_blocks_per_sm_cascaded();
 int batch_blocks_per_sm_bgk();
 int batch_blocks_per_sm_rawmrt();
@@ -39,6 +56,10 @@ struct lbm_batch_s {
     int graph_steps = 100;
     cudaGraphExec_t graph = nullptr;
     float tuned_ms = 0.f;
+    // Stochastic rounding: per-domain hashes of (seed, step) for the launches of
+    // a graph replay or a single launch, [doms][ncounters], filled before each.
+    unsigned* d_rtab = nullptr;
+    bool any_sr = false;
 };
 
 namespace {
@@ -100,6 +121,7 @@ cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int rows, int order) {
 cudaError_t refresh_domains(lbm_batch_s* b) {
     cudaError_t e = cudaEventSynchronize(b->done);  // the previous upload has finished reading h_doms
     if (e != cudaSuccess) return e;
+    bool any_sr = false;
     for (size_t i = 0; i < b->doms.size(); ++i) {
         const lbm_s* h = b->doms[i];
         BatchDomain& D = b->h_doms[i];
@@ -108,32 +130,45 @@ cudaError_t refresh_domains(lbm_batch_s* b) {
         D.walls = h->walls ? 1 : 0;
         D.force = lbm::force_mode(h);
         D.parity = int(h->t & 1);
+        D.t = h->t;
+        any_sr = any_sr || h->a.rseed != 0;
     }
+    b->any_sr = any_sr;
     return cudaMemcpyAsync(b->d_doms, b->h_doms, b->doms.size() * sizeof(BatchDomain), cudaMemcpyHostToDevice,
                            b->stream);
 }
 
-cudaError_t launch(lbm_batch_s* b, int flip, int* counter) {
+// Hashes for `count` launches that start `base` steps after the domains' counts.
+cudaError_t fill_round_table(lbm_batch_s* b, int count, long long base) {
+    if (!b->any_sr) return cudaSuccess;
+    const int n = int(b->doms.size()) * count;
+    lbm::fill_batch_round_table<<<(n + lbm::kBatchThreads - 1) / lbm::kBatchThreads, lbm::kBatchThreads, 0, b->stream>>>(
+        b->d_doms, int(b->doms.size()), b->d_rtab, count, base);
+    return cudaGetLastError();
+}
+
+// kstep: the launch's index in a sequence whose round table has rstride entries per domain.
+cudaError_t launch(lbm_batch_s* b, int flip, int* counter, int rstride, int kstep) {
     switch (b->model) {
         case LBM_CASCADED:
             return lbm::launch_batch_cascaded(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy,
-                                              counter, b->stream);
+                                              counter, b->d_rtab, rstride, kstep, b->stream);
         case LBM_BGK:
             return lbm::launch_batch_bgk(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy, counter,
-                                         b->stream);
+                                         b->d_rtab, rstride, kstep, b->stream);
         default:
             return lbm::launch_batch_rawmrt(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy,
-                                            counter, b->stream);
+                                            counter, b->d_rtab, rstride, kstep, b->stream);
     }
 }
 
-// One step outside a graph (the counter of the dynamic policy is reset first).
-cudaError_t launch_single(lbm_batch_s* b, int flip) {
-    if (b->policy == lbm::kPolicyDynamic) {
-        cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int), b->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return launch(b, flip, b->d_counters);
+// One step outside a graph, `base` steps after the domains' counts (the counter
+// of the dynamic policy is reset first).
+cudaError_t launch_single(lbm_batch_s* b, int flip, long long base) {
+    cudaError_t e = fill_round_table(b, 1, base);
+    if (e == cudaSuccess && b->policy == lbm::kPolicyDynamic) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) return e;
+    return launch(b, flip, b->d_counters, 1, 0);
 }
 
 void drop_graph(lbm_batch_s* b) {
@@ -147,7 +182,8 @@ cudaError_t build_graph(lbm_batch_s* b) {
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     if (b->policy == lbm::kPolicyDynamic) e = cudaMemsetAsync(b->d_counters, 0, b->graph_steps * sizeof(int), b->stream);
-    for (int k = 0; k < b->graph_steps && e == cudaSuccess; ++k) e = launch(b, k & 1, b->d_counters + k);
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; ++k)
+        e = launch(b, k & 1, b->d_counters + k, b->graph_steps, k);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -224,7 +260,6 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
         if (h->store != LBM_F32 && h->store != LBM_F16DEV && h->store != LBM_BF16DEV)
             return fail(LBM_EINVAL, "lbm_batch_create: storage must be LBM_F32, LBM_BF16DEV or LBM_F16DEV");
         if (h->has_field) return fail(LBM_EINVAL, "lbm_batch_create: per-node force fields are not batched");
-        if (h->a.rseed) return fail(LBM_EINVAL, "lbm_batch_create: stochastic rounding is not batched");
         for (int j = 0; j < i; ++j)
             if (lattices[j] == h) return fail(LBM_EINVAL, "lbm_batch_create: a lattice appears twice");
     }
@@ -252,6 +287,7 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_doms, count * sizeof(BatchDomain));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, b->tiles_cap * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, b->ncounters * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rtab, size_t(count) * b->ncounters * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) {
         b->grid = b->sms * blocks_per_sm(b->model);
@@ -273,6 +309,7 @@ int lbm_batch_destroy(lbm_batch_t b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_rtab) cudaFree(b->d_rtab);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_doms) cudaFree(b->d_doms);
     if (b->h_doms) cudaFreeHost(b->h_doms);
@@ -299,17 +336,18 @@ int lbm_batch_step(lbm_batch_t b, long n) {
     if (n == 0) return LBM_OK;
     Guard g(b->device);
     for (lbm_s* h : b->doms)
-        if (h->a.rseed || h->has_field)
-            return fail(LBM_EINVAL, "lbm_batch_step: a lattice now has stochastic rounding or a force field");
+        if (h->has_field) return fail(LBM_EINVAL, "lbm_batch_step: a lattice now has a per-node force field");
     BATCH_CUDA(wait_for_domains(b), "lbm_batch_step: waiting for the lattices' streams");
     BATCH_CUDA(refresh_domains(b), "lbm_batch_step: domain table");
     long done = 0;
     if (b->graph_steps > 0 && n >= b->graph_steps) {
         if (!b->graph) BATCH_CUDA(build_graph(b), "lbm_batch_step: graph capture");
-        for (; n - done >= b->graph_steps; done += b->graph_steps)
+        for (; n - done >= b->graph_steps; done += b->graph_steps) {
+            BATCH_CUDA(fill_round_table(b, b->graph_steps, done), "lbm_batch_step: round table");
             BATCH_CUDA(cudaGraphLaunch(b->graph, b->stream), "lbm_batch_step: graph launch");
+        }
     }
-    for (long k = done; k < n; ++k) BATCH_CUDA(launch_single(b, int((k - done) & 1)), "lbm_batch_step: launch");
+    for (long k = done; k < n; ++k) BATCH_CUDA(launch_single(b, int((k - done) & 1), k), "lbm_batch_step: launch");
     for (lbm_s* h : b->doms) h->t += n;
     BATCH_CUDA(release_domains(b), "lbm_batch_step: event");
     return LBM_OK;
@@ -360,9 +398,9 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
                 b->rows = rows;
                 b->order = order;
                 b->policy = policy;
-                for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_single(b, k & 1);
+                for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_single(b, k & 1, k);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
-                for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_single(b, k & 1);
+                for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_single(b, k & 1, k);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 float ms = 0.f;

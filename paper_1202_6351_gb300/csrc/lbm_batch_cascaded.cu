@@ -3,8 +3,9 @@
 
 namespace lbm {
 cudaError_t launch_batch_cascaded(int grid, const BatchDomain* doms, const int* tiles, int ntiles, int lbx, int rows, int flip,
-                            int policy, int* counter, cudaStream_t s) {
-    batch_kernel<LBM_CASCADED><<<grid, kBatchThreads, 0, s>>>(doms, tiles, ntiles, lbx, rows, flip, policy, counter);
+                            int policy, int* counter, const unsigned* rtab, int rstride, int kstep,
+                            cudaStream_t s) {
+    batch_kernel<LBM_CASCADED><<<grid, kBatchThreads, 0, s>>>(doms, tiles, ntiles, lbx, rows, flip, policy, counter, rtab, rstride, kstep);
     return cudaGetLastError();
 }
 int batch_blocks_per_sm_cascaded() {

@@ -23,25 +23,33 @@ struct BatchDomain {
     int walls;   // any non-periodic edge
     int force;   // 0: none, 1: uniform
     int parity;  // AA parity of the domain's next step when the launch sequence starts
+    long long t; // the domain's step count when the launch sequence starts (stochastic rounding)
 };
 
-template <int MODEL, int STORE, bool ODD>
-__device__ __forceinline__ void batch_node_store(const BatchDomain& D, int x, int y) {
+template <int MODEL, int STORE, bool ODD, bool SR>
+__device__ __forceinline__ void batch_node_store(const BatchDomain& D, int x, int y, unsigned rb) {
     if (D.walls) {
-        if (D.force) step_node_split<MODEL, STORE, ODD, 1, true>(D.a, x, y);
-        else step_node_split<MODEL, STORE, ODD, 0, true>(D.a, x, y);
+        if (D.force) step_node_split<MODEL, STORE, ODD, 1, true, SR>(D.a, x, y, rb);
+        else step_node_split<MODEL, STORE, ODD, 0, true, SR>(D.a, x, y, rb);
     } else {
-        if (D.force) step_node<MODEL, STORE, ODD, 1, false>(D.a, x, y);
-        else step_node<MODEL, STORE, ODD, 0, false>(D.a, x, y);
+        if (D.force) step_node<MODEL, STORE, ODD, 1, false, SR>(D.a, x, y, rb);
+        else step_node<MODEL, STORE, ODD, 0, false, SR>(D.a, x, y, rb);
     }
 }
 
+// rb: the hash of (seed, step) of a domain with stochastic rounding (D.a.rseed).
 template <int MODEL, bool ODD>
-__device__ __forceinline__ void batch_node(const BatchDomain& D, int x, int y) {
+__device__ __forceinline__ void batch_node(const BatchDomain& D, int x, int y, unsigned rb) {
     switch (D.store) {
-        case LBM_F32: batch_node_store<MODEL, LBM_F32, ODD>(D, x, y); break;
-        case LBM_F16DEV: batch_node_store<MODEL, LBM_F16DEV, ODD>(D, x, y); break;
-        default: batch_node_store<MODEL, LBM_BF16DEV, ODD>(D, x, y); break;
+        case LBM_F32: batch_node_store<MODEL, LBM_F32, ODD, false>(D, x, y, 0u); break;
+        case LBM_F16DEV:
+            if (D.a.rseed) batch_node_store<MODEL, LBM_F16DEV, ODD, true>(D, x, y, rb);
+            else batch_node_store<MODEL, LBM_F16DEV, ODD, false>(D, x, y, 0u);
+            break;
+        default:
+            if (D.a.rseed) batch_node_store<MODEL, LBM_BF16DEV, ODD, true>(D, x, y, rb);
+            else batch_node_store<MODEL, LBM_BF16DEV, ODD, false>(D, x, y, 0u);
+            break;
     }
 }
 
@@ -51,7 +59,9 @@ __device__ __forceinline__ void batch_node(const BatchDomain& D, int x, int y) {
 template <int MODEL>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchDomain* __restrict__ doms,
                                                               const int* __restrict__ tiles, int ntiles, int lbx,
-                                                              int rows, int flip, int policy, int* counter) {
+                                                              int rows, int flip, int policy, int* counter,
+                                                              const unsigned* __restrict__ rtab, int rstride,
+                                                              int kstep) {
     __shared__ int s_next;
     const int bx = 1 << lbx, by = kBatchThreads >> lbx;
     const int lx = threadIdx.x & (bx - 1), ly = threadIdx.x >> lbx;
@@ -77,12 +87,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchDomain*
         const BatchDomain& D = doms[dom];
         const int x = tiles[3 * t + 1] * bx + lx, y0 = tiles[3 * t + 2] * by * rows + ly;
         const bool odd = ((D.parity ^ flip) & 1) != 0;
+        const unsigned rb = D.a.rseed ? rtab[dom * rstride + kstep] : 0u;
         if (x < D.a.nx) {
             for (int r = 0; r < rows; ++r) {
                 const int y = y0 + r * by;
                 if (y >= D.a.ny) break;
-                if (odd) batch_node<MODEL, true>(D, x, y);
-                else batch_node<MODEL, false>(D, x, y);
+                if (odd) batch_node<MODEL, true>(D, x, y, rb);
+                else batch_node<MODEL, false>(D, x, y, rb);
             }
         }
         if (policy != kPolicyDynamic) t += stride;

@@ -269,14 +269,16 @@ __device__ __forceinline__ unsigned round_node(const Args& a, unsigned base, int
 }
 
 // Store the nine post-collision deviations of node (x, y).
+// rb: the hash C0 of this launch's (seed, step) when SR (stochastic rounding).
 template <int STORE, bool ODD, bool WALLS, bool SR = false>
-__device__ __forceinline__ void store_node(const Args& a, int x, int y, const typename Store<STORE>::R d[9]) {
+__device__ __forceinline__ void store_node(const Args& a, int x, int y, const typename Store<STORE>::R d[9],
+                                           unsigned rb) {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     T* __restrict__ f = static_cast<T*>(a.f);
     const int n = y * a.pitch + x;
-    const unsigned rn = SR ? round_node(a, round_base(a), x, y) : 0u;
+    const unsigned rn = SR ? round_node(a, rb, x, y) : 0u;
     auto enc = [&](R v, int q) -> T { return SR ? enc_sr<STORE>(v, rn + static_cast<unsigned>(q) * kRoundStride) : S::enc(v); };
     if (!ODD) {
 #pragma unroll
@@ -519,7 +521,7 @@ LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
 // ---------------------------------------------------------------- one node, one step
 // a1-a9: AA-pattern load, decode, force, collision, encode, AA-pattern store.
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false>
-__device__ __forceinline__ void step_node(const Args& a, int x, int y) {
+__device__ __forceinline__ void step_node(const Args& a, int x, int y, unsigned rb) {
     using R = typename Store<STORE>::R;
     const Coef<R> c(a);
     R d[9];
@@ -527,17 +529,18 @@ __device__ __forceinline__ void step_node(const Args& a, int x, int y) {
     R Fx, Fy;
     node_force<R, FORCE>(a, x, y, Fx, Fy);
     collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
-    store_node<STORE, ODD, WALLS, SR>(a, x, y, d);
+    store_node<STORE, ODD, WALLS, SR>(a, x, y, d, rb);
 }
 
 // As step_node; with walls, only nodes on the lattice edge take the wall-aware
-// path (an interior node has no wall link and no wrapped neighbour).
+// path (an interior node has no wall link and no wrapped neighbour).  rb as in
+// store_node (ignored unless SR).
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false>
-__device__ __forceinline__ void step_node_split(const Args& a, int x, int y) {
+__device__ __forceinline__ void step_node_split(const Args& a, int x, int y, unsigned rb = 0u) {
     if (WALLS && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)))
-        step_node<MODEL, STORE, ODD, FORCE, true, SR>(a, x, y);
+        step_node<MODEL, STORE, ODD, FORCE, true, SR>(a, x, y, rb);
     else
-        step_node<MODEL, STORE, ODD, FORCE, false, SR>(a, x, y);
+        step_node<MODEL, STORE, ODD, FORCE, false, SR>(a, x, y, rb);
 }
 
 }  // namespace lbm

@@ -92,8 +92,8 @@ __device__ __forceinline__ void step_pair(const Args& a, int x, int y, bool two)
     collide<MODEL, F2, (FORCE != 0)>(d, F2(make_float2(fx0, fx1)), F2(make_float2(fy0, fy1)), c);
 #pragma unroll
     for (int q = 0; q < 9; ++q) { d0[q] = d[q].v.x; d1[q] = d[q].v.y; }
-    store_node<STORE, ODD, false>(a, x, y, d0);
-    if (two) store_node<STORE, ODD, false>(a, x, y + 1, d1);
+    store_node<STORE, ODD, false>(a, x, y, d0, 0u);
+    if (two) store_node<STORE, ODD, false>(a, x, y + 1, d1, 0u);
 }
 
 }  // namespace lbm

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y);
+    step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y, SR ? round_base(a) : 0u);
 }
 
 // Two rows per thread (nodes (x, y) and (x, y + 1)) with packed FP32x2
@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kStepBX * kStepBY, ODD ? 4 : 3) step_kernel_ve
         step_vec<N, MODEL, STORE, ODD, FORCE, SR>(a, x0, y, vmask, threadIdx.x & 31);
     } else if (inside) {
         const int x1 = min(x0 + N, a.nx);
-        for (int x = x0; x < x1; ++x) step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y);
+        const unsigned rb = SR ? round_base(a) : 0u;
+        for (int x = x0; x < x1; ++x) step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y, rb);
     }
 }
 

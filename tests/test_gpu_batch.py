@@ -51,10 +51,22 @@ def make(spec, seed):
     return L
 
 
+def with_rounding(L, i):
+    """Stochastic rounding on the 16-bit lattices except domain 3 (seed = index)."""
+    if L.store in (lbm.F16DEV, lbm.BF16DEV) and i != 3:
+        L.set_rounding(lbm.ROUND_STOCHASTIC, i)
+    return L
+
+
+@pytest.mark.parametrize("rounding", [False, True], ids=["nearest", "mixed_stochastic"])
 @pytest.mark.parametrize("tune", [False, True], ids=["default", "tuned"])
-def test_batch_is_bitwise_equal_to_single_lattice_steps(tune):
+def test_batch_is_bitwise_equal_to_single_lattice_steps(tune, rounding):
     alone = [make(s, i) for i, s in enumerate(DOMAINS)]
     batched = [make(s, i) for i, s in enumerate(DOMAINS)]
+    if rounding:  # the batch's per-domain round table must reproduce lbm_step's hashes
+        alone = [with_rounding(L, i) for i, L in enumerate(alone)]
+        batched = [with_rounding(L, i) for i, L in enumerate(batched)]
+        assert {L.store for i, L in enumerate(batched) if L.store != lbm.F32 and i != 3} == {lbm.F16DEV, lbm.BF16DEV}
     # start two lattices one step ahead: the batch handles mixed parities
     for k in (1, 4):
         alone[k].step(1)

@@ -500,8 +500,6 @@ def test_stochastic_rounding_keeps_mass_and_rejects_misuse(store):
     assert abs(m1 - m0) / m0 <= (2e-6 if store == lbm.F16DEV else 2e-5)
     with pytest.raises(lbm.LBMError):
         g.set_rounding(5)
-    with pytest.raises(lbm.LBMError):
-        lbm.Batch([g])
     g.set_rounding(lbm.ROUND_NEAREST)
     g.close()
     f32 = lbm.Lattice(16, 16, OMEGAS, store=lbm.F32)
