@@ -20,8 +20,10 @@
 // place.  After an even number of steps slot a of node x holds f_a(x).
 // Half-way bounce-back: a link whose far end lies beyond a wall is reflected
 // at the node itself, with the moving-wall term 6 w_a rho_w (e_a . U_wall)
-// (Sec. III-C); a link leaving through a south/north wall is decided by that
-// wall even when it also leaves in x.
+// (Sec. III-C); a diagonal link through the corner point of two walls is
+// reflected without it (see incoming_wall).
+// The 16-bit stores round to nearest even or, per lattice, stochastically
+// (StochasticRound, random offsets from a counter-based hash).
 #pragma once
 
 #include <cuda_bf16.h>
