@@ -7,7 +7,8 @@ one launch of the fused stream-and-collide kernel.  The populations (4096^2 x
 9 x 4 B = 604 MB in FP32) are far larger than L2, so no flush is needed.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+instead, one single-threaded process per host core, each on a bounded sample
+of the same workload.
 """
 from __future__ import annotations
 

@@ -86,3 +86,26 @@ def test_null_handles():
     assert lib.lbm_time(None) == -1
     out = (C.c_double * 3)()
     assert lib.lbm_stats(None, out) == lbm.LBM_EINVAL
+
+
+def test_null_handles_of_the_tuning_rounding_batch_and_adjoint_calls():
+    """Every entry point answers a NULL handle with LBM_EINVAL before touching
+    the device (here there is none: a CUDA call would give LBM_ECUDA)."""
+    lib = lbm.load_library()
+    ms = (C.c_float * 3)()
+    assert lib.lbm_set_variant(None, 0) == lbm.LBM_EINVAL
+    assert lib.lbm_set_rounding(None, lbm.ROUND_STOCHASTIC, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_tune(None, 4, ms) == lbm.LBM_EINVAL
+    assert lib.lbm_set_graph_steps(None, 8) == lbm.LBM_EINVAL
+    assert lib.lbm_set_check(None, 10, 1e-3) == lbm.LBM_EINVAL
+    assert lib.lbm_adjoint_run(None, 10, 5, None, None, None, None, None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_destroy(None) == lbm.LBM_OK
+    assert lib.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_tune(None, 1, None) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_sync(None) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_set_graph_steps(None, 8) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_info(None, None, None) == lbm.LBM_EINVAL
+    out = C.c_void_p()
+    assert lib.lbm_batch_create(None, 0, C.byref(out)) == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error()
+
