@@ -42,6 +42,11 @@ def _corner_symmetry():
     T.test_cavity_is_equivariant_under_a_quarter_turn(O.CASCADED)
 
 
+def _strain_divergence():
+    for om in ((1.3, 1.6, 1.6, 1.0, 1.0, 1.0), (1.6, 1.3, 1.3, 1.0, 1.0, 1.0)):
+        T.test_strain_divergence_satisfies_continuity(om)
+
+
 def _unit_rates():
     T.test_unit_rates_give_the_cascaded_equilibrium()
 
@@ -65,6 +70,8 @@ MUTATIONS = [
     ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
     ("lid term on the links through a corner", "if (!corner && L->edge[wall] == ORACLE_MOVING_WALL)",
      "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),
+    ("omega_4 in place of omega_3 in the strain divergence (Eq. 28)", "const real div = -1.5 * om[0] * n3;",
+     "const real div = -1.5 * om[1] * n3;", _strain_divergence),
     ("transposed K in the raw-MRT projection", "m += KMAT[a][b] * fb[a];", "m += KMAT[b][a] * fb[a];",
      _mrt),
     ("omega_3 used for the deviatoric kernel", "(w4 / 4.0) * (rho * (ux * ux - uy * uy)",
