@@ -47,6 +47,11 @@ def _strain_divergence():
         T.test_strain_divergence_satisfies_continuity(om)
 
 
+def _force_field():
+    for m in (O.CASCADED, O.BGK, O.RAWMRT):
+        T.test_force_field_adds_to_the_uniform_force(m)
+
+
 def _unit_rates():
     T.test_unit_rates_give_the_cascaded_equilibrium()
 
@@ -72,6 +77,8 @@ MUTATIONS = [
      "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),
     ("omega_4 in place of omega_3 in the strain divergence (Eq. 28)", "const real div = -1.5 * om[0] * n3;",
      "const real div = -1.5 * om[1] * n3;", _strain_divergence),
+    ("force field replaces the uniform force", "F[0] += L->force_field[node];", "F[0] = L->force_field[node];",
+     _force_field),
     ("transposed K in the raw-MRT projection", "m += KMAT[a][b] * fb[a];", "m += KMAT[b][a] * fb[a];",
      _mrt),
     ("omega_3 used for the deviatoric kernel", "(w4 / 4.0) * (rho * (ux * ux - uy * uy)",

@@ -389,6 +389,31 @@ def test_strain_divergence_satisfies_continuity(om):
     assert np.abs(div + ddt).max() <= 0.05 * np.abs(ddt).max()
 
 
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_force_field_adds_to_the_uniform_force(model):
+    """A per-node force field equal to a constant F acts as the uniform force F,
+    and a field adds to the uniform force (reading 16): three ways of applying
+    the same total force give the same run."""
+    nx, ny = 9, 7
+    om = (1.2, 1.6, 1.5, 0.9, 1.1, 1.3)
+    rng = np.random.default_rng(21)
+    rho, u = 1 + 0.01 * rng.standard_normal((ny, nx)), 0.02 * rng.standard_normal((2, ny, nx))
+    F = (3e-5, -2e-5)
+    field = np.stack([np.full((ny, nx), F[0]), np.full((ny, nx), F[1])])
+    runs = [
+        O.Lattice(nx, ny, om, force=F, model=model),
+        O.Lattice(nx, ny, om, force_field=field, model=model),
+        O.Lattice(nx, ny, om, force=(F[0] / 2, 0.0), force_field=field - np.array([F[0] / 2, 0.0])[:, None, None],
+                  model=model),
+    ]
+    out = [L.init(rho, u).run(12).f.copy() for L in runs]
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out[2], out[0], rtol=0, atol=1e-15)
+    # and a force changes the run (the field is not ignored)
+    free = O.Lattice(nx, ny, om, model=model).init(rho, u).run(12).f
+    assert np.abs(free - out[0]).max() > 1e-6
+
+
 def _tg_run(n, om=1.6, periods=1.0):
     nu = O.nu_from_omega(om)
     u0 = 0.04 * 64 / n
