@@ -30,7 +30,7 @@ def _streaming():
 
 
 def _couette():
-    T.test_couette_moving_wall(O.CASCADED, 1e-12)
+    T.test_couette_moving_wall(O.CASCADED)
 
 
 def _conservation():

@@ -403,18 +403,26 @@ def test_poiseuille_wall_slip_cascaded(om, steps):
     assert 600 < errs[0] / errs[1] < 1600
 
 
-@pytest.mark.parametrize("model,tol", [(O.CASCADED, 1e-12), (O.BGK, 1e-10), (O.RAWMRT, 5e-4)])
-def test_couette_moving_wall(model, tol):
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_couette_moving_wall(model):
     """Plane Couette flow: fixed south wall, north wall moving at U; the steady
-    profile is linear, u(y) = U (y + 1/2) / H between the half-way walls."""
+    profile is linear, U (y + 1/2) / H between the half-way walls.  Which
+    quantity is exactly linear depends on what the odd moments relax about: the
+    cascaded collision relaxes central moments about u, so u is; raw MRT relaxes
+    raw moments towards equilibria of j = rho u, so j is, while rho varies across
+    the channel at O(U^2) (u then deviates by about 1e-5 of U); BGK also keeps
+    rho uniform."""
     U, om, H = 0.05, 1.2, 16
     L = O.Lattice(3, H, (1, om, om, 1, 1, 1),
                   edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.MOVING_WALL), wall_u=(0, 0, 0, U),
                   model=model)
     L.init().run(20000)
-    _, u = L.macros()
+    rho, u = L.macros()
     ua = U * (np.arange(H) + 0.5) / H
-    assert np.abs(u[0][:, 0] - ua).max() / U < tol
+    q = u[0] if model == O.CASCADED else rho * u[0]
+    assert np.abs(q[:, 0] - ua).max() / U < 1e-12
+    if model == O.RAWMRT:
+        assert 1e-6 < np.ptp(rho) < 1e-4
     s = L.strain()
     np.testing.assert_allclose(s[2], U / H, rtol=2e-2 if model == O.RAWMRT else 1e-6)
 
