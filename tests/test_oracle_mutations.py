@@ -52,6 +52,10 @@ def _force_field():
         T.test_force_field_adds_to_the_uniform_force(m)
 
 
+def _sound_wave():
+    T.test_standing_sound_wave_speed_and_damping(O.CASCADED, T.SOUND_RATES[0])
+
+
 def _unit_rates():
     T.test_unit_rates_give_the_cascaded_equilibrium()
 
@@ -81,6 +85,8 @@ MUTATIONS = [
      _force_field),
     ("transposed K in the raw-MRT projection", "m += KMAT[a][b] * fb[a];", "m += KMAT[b][a] * fb[a];",
      _mrt),
+    ("omega_4 used for the bulk kernel", "const real g3 = (w3 / 12.0)", "const real g3 = (w4 / 12.0)",
+     _sound_wave),
     ("omega_3 used for the deviatoric kernel", "(w4 / 4.0) * (rho * (ux * ux - uy * uy)",
      "(w3 / 4.0) * (rho * (ux * ux - uy * uy)", _relaxation_identity),
 ]

@@ -403,6 +403,41 @@ def test_poiseuille_wall_slip_cascaded(om, steps):
     assert 600 < errs[0] / errs[1] < 1600
 
 
+SOUND_RATES = [(1.6, 1.0, 1.0, 1.0, 1.0, 1.0), (0.8, 1.6, 1.6, 1.2, 0.9, 1.3)]
+
+
+@pytest.mark.parametrize("om", SOUND_RATES)
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_standing_sound_wave_speed_and_damping(model, om):
+    """Linear acoustics: a density wave rho = 1 + eps cos(k x) released at rest
+    oscillates as A e^{-Gamma t} cos(Omega t + phi) with Gamma = k^2 (nu + zeta)/2
+    and Omega = sqrt(c_s^2 k^2 - Gamma^2), c_s^2 = 1/3, shear viscosity
+    nu = (1/omega_4 - 1/2)/3 and bulk viscosity zeta = (1/omega_3 - 1/2)/3 (the
+    trace of the second-order moments relaxes at omega_3; BGK has the single
+    rate omega_4 for both).  Lattice corrections are O(k^2) relative: a few
+    1e-4 at 128 nodes per wavelength."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    nx, ny, eps = 128, 2, 1e-4
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    L = O.Lattice(nx, ny, om, model=model).init(np.tile(1 + eps * np.cos(k * x), (ny, 1)),
+                                                np.zeros((2, ny, nx)))
+    amp = []
+    for _ in range(3000):
+        rho, _ = L.macros()
+        amp.append(2 / nx * ((rho[0] - 1) * np.cos(k * x)).sum())
+        L.run(1)
+    amp, t = np.array(amp), np.arange(len(amp))
+    w3 = om[1] if model == O.BGK else om[0]
+    gamma = k * k * ((1 / om[1] - 0.5) + (1 / w3 - 0.5)) / 6
+    omega = math.sqrt(k * k / 3 - gamma ** 2)
+    wave = lambda t, A, G, W, p: A * np.exp(-G * t) * np.cos(W * t + p)  # noqa: E731
+    p, _ = scipy_opt.curve_fit(wave, t, amp, p0=[eps, gamma, omega, 0.0])
+    assert np.abs(wave(t, *p) - amp).max() < 1e-5 * eps
+    assert abs(p[1] / gamma - 1) < 2e-3
+    assert abs(p[2] / omega - 1) < 1e-3
+
+
 @pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
 def test_couette_moving_wall(model):
     """Plane Couette flow: fixed south wall, north wall moving at U; the steady
