@@ -349,30 +349,38 @@ def test_poiseuille_channel(model):
     assert np.abs(u[0] - u[0][:, :1]).max() < 1e-15
 
 
-def _channel_momentum(model, om, umax, steps, H=32):
-    """Steady x-momentum rho u_x per row of a forced channel, and the closed form.
+def _channel_momentum(model, om, umax, steps, axis=0, H=32):
+    """Steady momentum along the channel per cross-channel row, and the closed form.
 
-    Closed form: in an x-invariant steady channel flow the part of f that is odd
-    in e_x carries three moments per row, j_x, P = sum e_x e_y f and
-    Q = sum e_x e_y^2 f.  P relaxes with the shear rate w_p (omega_5; omega_4 for
-    BGK), Q with w_q (omega_7, the x y^2 moment; omega_4 for BGK) towards j_x / 3,
-    and the source S of Eq. 14 has no x y^2 moment when u_y = F_y = 0.  A
-    quadratic j_x, linear P and quadratic Q then satisfy pull streaming, the
-    collision and half-way bounce-back exactly, with j_x = B y (H - y) + u_s,
-    where y = j + 1/2 is the distance to the wall, B = F_x / (2 nu) and
-    u_s = B (2 Lambda - 1/4), Lambda = (1/w_p - 1/2)(1/w_q - 1/2)."""
+    Closed form (axis 0: flow along x, walls at y = -1/2 and H - 1/2): in an
+    x-invariant steady channel flow the part of f that is odd in e_x carries
+    three moments per row, j_x, P = sum e_x e_y f and Q = sum e_x e_y^2 f.  P
+    relaxes with the shear rate w_p (omega_5; omega_4 for BGK), Q with w_q
+    (omega_7, the x y^2 moment; omega_4 for BGK) towards j_x / 3, and the source
+    S of Eq. 14 has no x y^2 moment when u_y = F_y = 0.  A quadratic j_x, linear
+    P and quadratic Q then satisfy pull streaming, the collision and half-way
+    bounce-back exactly, with j_x = B y (H - y) + u_s, where y = j + 1/2 is the
+    distance to the wall, B = F_x / (2 nu) and u_s = B (2 Lambda - 1/4),
+    Lambda = (1/w_p - 1/2)(1/w_q - 1/2).  Axis 1 is the same flow turned a
+    quarter: along y between walls at x, where the third-order moment is x^2 y
+    and w_q is omega_6."""
     w_p = om[1] if model == O.BGK else om[2]
-    w_q = om[1] if model == O.BGK else om[4]
+    w_q = om[1] if model == O.BGK else om[4 - axis]
     nu = O.nu_from_omega(w_p)
-    fx = 8 * nu * umax / H ** 2
-    L = O.Lattice(4, H, om, force=(fx, 0),
-                  edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK), model=model)
+    f = 8 * nu * umax / H ** 2
+    if axis == 0:
+        L = O.Lattice(4, H, om, force=(f, 0),
+                      edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK), model=model)
+    else:
+        L = O.Lattice(H, 4, om, force=(0, f),
+                      edges=(O.BOUNCEBACK, O.BOUNCEBACK, O.PERIODIC, O.PERIODIC), model=model)
     L.init().run(steps)
     rho, u = L.macros()
-    B = fx / (2 * nu)
+    j = (rho * u[0])[:, 0] if axis == 0 else (rho * u[1])[0, :]
+    B = f / (2 * nu)
     lam = (1 / w_p - 0.5) * (1 / w_q - 0.5)
     y = np.arange(H) + 0.5
-    return (rho * u[0])[:, 0], B * y * (H - y) + B * (2 * lam - 0.25)
+    return j, B * y * (H - y) + B * (2 * lam - 0.25)
 
 
 # Rates with omega_4 != omega_5 and omega_6 != omega_7, so a swapped rate index
@@ -380,16 +388,18 @@ def _channel_momentum(model, om, umax, steps, H=32):
 SLIP_CASES = [((1.0, 0.7, 0.7, 1.5, 0.8, 1.0), 12000), ((1.2, 1.3, 0.7, 0.8, 1.6, 1.1), 40000)]
 
 
+@pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("om,steps", SLIP_CASES)
 @pytest.mark.parametrize("model", [O.BGK, O.RAWMRT])
-def test_poiseuille_wall_slip_closed_form(model, om, steps):
+def test_poiseuille_wall_slip_closed_form(model, om, steps, axis):
     """BGK and raw MRT: the steady channel is the shifted parabola exactly."""
-    j, ja = _channel_momentum(model, om, 0.01, steps)
+    j, ja = _channel_momentum(model, om, 0.01, steps, axis)
     assert np.abs(j - ja).max() < 1e-9 * 0.01
 
 
+@pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("om,steps", SLIP_CASES)
-def test_poiseuille_wall_slip_cascaded(om, steps):
+def test_poiseuille_wall_slip_cascaded(om, steps, axis):
     """The cascaded collision relaxes the central x y^2 moment, which adds to Q
     u_x times the non-equilibrium part of sum e_y^2 f; that part is quadratic in
     u, so the added term is of third order in U.  The cascaded channel meets the
@@ -397,7 +407,7 @@ def test_poiseuille_wall_slip_cascaded(om, steps):
     tenfold."""
     errs = []
     for umax in (1e-2, 1e-3):
-        j, ja = _channel_momentum(O.CASCADED, om, umax, steps)
+        j, ja = _channel_momentum(O.CASCADED, om, umax, steps, axis)
         errs.append(np.abs(j - ja).max())
     assert errs[0] < 1e-6 * 1e-2
     assert 600 < errs[0] / errs[1] < 1600
