@@ -30,7 +30,11 @@ def _streaming():
 
 
 def _couette():
-    T.test_couette_moving_wall(O.CASCADED)
+    T.test_couette_moving_wall(O.CASCADED, "north")
+
+
+def _couette_east():
+    T.test_couette_moving_wall(O.CASCADED, "east")
 
 
 def _conservation():
@@ -76,6 +80,9 @@ MUTATIONS = [
     ("wrong sign of m4 in S4", "(-6.0 * m2 - m3 - 9.0 * m4", "(-6.0 * m2 - m3 + 9.0 * m4", _source_moments),
     ("wrong rest target of xxyy", "(1.0 / 9.0) * rho + 3.0", "(1.0 / 3.0) * rho + 3.0", _unit_rates),
     ("lid correction with the wrong sign", "corr = 6.0 * W[b]", "corr = -6.0 * W[b]", _couette),
+    ("west and east wall speeds taken along x",
+     "(wall >= 2) ? L->wall_u[wall] : 0.0;\n                        const real Uy = (wall >= 2) ? 0.0 : L->wall_u[wall];",
+     "L->wall_u[wall];\n                        const real Uy = 0.0;", _couette_east),
     ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
     ("lid term on the links through a corner", "if (!corner && L->edge[wall] == ORACLE_MOVING_WALL)",
      "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),

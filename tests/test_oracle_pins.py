@@ -448,28 +448,44 @@ def test_standing_sound_wave_speed_and_damping(model, om):
     assert abs(p[2] / omega - 1) < 1e-3
 
 
+# Moving wall -> (edges W E S N, wall speeds, velocity component, flow along x?,
+# wall at the far end of the cross-channel axis?): the other wall is at rest.
+COUETTE_WALLS = {
+    "north": ((O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.MOVING_WALL), (0, 0, 0, 1), True, True),
+    "south": ((O.PERIODIC, O.PERIODIC, O.MOVING_WALL, O.BOUNCEBACK), (0, 0, 1, 0), True, False),
+    "east": ((O.BOUNCEBACK, O.MOVING_WALL, O.PERIODIC, O.PERIODIC), (0, 1, 0, 0), False, True),
+    "west": ((O.MOVING_WALL, O.BOUNCEBACK, O.PERIODIC, O.PERIODIC), (1, 0, 0, 0), False, False),
+}
+
+
+@pytest.mark.parametrize("wall", list(COUETTE_WALLS))
 @pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
-def test_couette_moving_wall(model):
-    """Plane Couette flow: fixed south wall, north wall moving at U; the steady
-    profile is linear, U (y + 1/2) / H between the half-way walls.  Which
-    quantity is exactly linear depends on what the odd moments relax about: the
-    cascaded collision relaxes central moments about u, so u is; raw MRT relaxes
-    raw moments towards equilibria of j = rho u, so j is, while rho varies across
-    the channel at O(U^2) (u then deviates by about 1e-5 of U); BGK also keeps
-    rho uniform."""
+def test_couette_moving_wall(model, wall):
+    """Plane Couette flow between a wall at rest and a wall moving at U along
+    itself; the steady profile is linear, U (d + 1/2) / H at d nodes from the
+    resting wall, between half-way walls.  Which quantity is exactly linear
+    depends on what the odd moments relax about: the cascaded collision relaxes
+    central moments about u, so u is; raw MRT relaxes raw moments towards
+    equilibria of j = rho u, so j is, while rho varies across the channel at
+    O(U^2) (u then deviates by about 1e-5 of U); BGK also keeps rho uniform.
+    Each of the four edges takes its turn as the moving wall."""
+    edges, speeds, along_x, far = COUETTE_WALLS[wall]
     U, om, H = 0.05, 1.2, 16
-    L = O.Lattice(3, H, (1, om, om, 1, 1, 1),
-                  edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.MOVING_WALL), wall_u=(0, 0, 0, U),
+    shape = (3, H) if along_x else (H, 3)
+    L = O.Lattice(*shape, (1, om, om, 1, 1, 1), edges=edges, wall_u=tuple(U * c for c in speeds),
                   model=model)
     L.init().run(20000)
     rho, u = L.macros()
-    ua = U * (np.arange(H) + 0.5) / H
-    q = u[0] if model == O.CASCADED else rho * u[0]
-    assert np.abs(q[:, 0] - ua).max() / U < 1e-12
+    q = u if model == O.CASCADED else rho * u
+    prof = q[0][:, 0] if along_x else q[1][0, :]
+    d = np.arange(H) if far else np.arange(H)[::-1]
+    assert np.abs(prof - U * (d + 0.5) / H).max() / U < 1e-12
+    cross = q[1] if along_x else q[0]
+    assert np.abs(cross).max() < 1e-13
     if model == O.RAWMRT:
         assert 1e-6 < np.ptp(rho) < 1e-4
-    s = L.strain()
-    np.testing.assert_allclose(s[2], U / H, rtol=2e-2 if model == O.RAWMRT else 1e-6)
+    shear = L.strain()[2]
+    np.testing.assert_allclose(shear, (1 if far else -1) * U / H, rtol=2e-2 if model == O.RAWMRT else 1e-6)
 
 
 @pytest.mark.parametrize("om", [(1.3, 1.6, 1.6, 1.0, 1.0, 1.0), (1.6, 1.3, 1.3, 1.0, 1.0, 1.0)])
