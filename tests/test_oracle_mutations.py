@@ -37,6 +37,10 @@ def _couette_east():
     T.test_couette_moving_wall(O.CASCADED, "east")
 
 
+def _init():
+    T.test_init_is_the_transformed_equilibrium(O.CASCADED)
+
+
 def _conservation():
     for m in (O.CASCADED, O.BGK, O.RAWMRT):
         T.test_collision_conserves_mass_and_adds_force(m)
@@ -83,6 +87,8 @@ MUTATIONS = [
     ("west and east wall speeds taken along x",
      "(wall >= 2) ? L->wall_u[wall] : 0.0;\n                        const real Uy = (wall >= 2) ? 0.0 : L->wall_u[wall];",
      "L->wall_u[wall];\n                        const real Uy = 0.0;", _couette_east),
+    ("start state shifted by +S/2", "f[a * plane + n] = feq[a] - 0.5 * S[a];",
+     "f[a * plane + n] = feq[a] + 0.5 * S[a];", _init),
     ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
     ("lid term on the links through a corner", "if (!corner && L->edge[wall] == ORACLE_MOVING_WALL)",
      "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),

@@ -513,6 +513,36 @@ def test_strain_divergence_satisfies_continuity(om):
 
 
 @pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_init_is_the_transformed_equilibrium(model):
+    """Eq. 6 and 12: the start state is f_bar = f_eq(rho, u) - S/2 with the force
+    acting at each node (uniform plus field), so Eq. 26-27 return the requested
+    rho and u, and f_bar + S/2 has the equilibrium moments: the central moments
+    of Eq. 10 for the cascaded model, those of the second-order polynomial
+    equilibrium for BGK and raw MRT."""
+    nx, ny = 5, 4
+    rng = np.random.default_rng(23)
+    rho = 1 + 0.05 * rng.standard_normal((ny, nx))
+    u = 0.05 * rng.standard_normal((2, ny, nx))
+    F = np.array([2e-3, -1e-3])
+    field = 1e-3 * rng.standard_normal((2, ny, nx))
+    L = O.Lattice(nx, ny, OMEGA_SETS[1], force=tuple(F), force_field=field, model=model).init(rho, u)
+    r, v = L.macros()
+    np.testing.assert_allclose(r, rho, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(v, u, rtol=0, atol=1e-15)
+    for y in range(ny):
+        for x in range(nx):
+            Fn = F + field[:, y, x]
+            ux, uy = u[:, y, x]
+            f = L.f[:, y, x] + O.source_node([ux, uy], Fn) / 2
+            if model == O.CASCADED:
+                expect = rho[y, x] * np.array([1, 0, 0, 1 / 3, 1 / 3, 0, 0, 0, 1 / 9])
+                np.testing.assert_allclose(P.central_moments(f, ux, uy), expect, rtol=0, atol=1e-15)
+            else:
+                np.testing.assert_allclose(f, O.equilibrium_node(O.BGK, rho[y, x], ux, uy), rtol=0, atol=1e-15)
+    assert np.abs(L.f[:, 0, 0] - O.equilibrium_node(model, rho[0, 0], *u[:, 0, 0])).max() > 1e-5
+
+
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
 def test_force_field_adds_to_the_uniform_force(model):
     """A per-node force field equal to a constant F acts as the uniform force F,
     and a field adds to the uniform force (reading 16): three ways of applying
