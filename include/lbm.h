@@ -191,7 +191,9 @@ int lbm_macros_device(lbm_t h, double* rho, double* u);
 
 /* Local strain-rate quantities from the non-equilibrium moments of
  * f = f_bar + S/2, Eq. (28)-(30) solved exactly for the two normal
- * components: out [3][ny][nx] = (d_x j_x, d_y j_y, d_x j_y + d_y j_x). */
+ * components: out [3][ny][nx] = (d_x j_x, d_y j_y, d_x j_y + d_y j_x).  The
+ * inversion divides by the rates at which the model relaxes the second-order
+ * moments: omega_3, omega_4, omega_5 (cascaded, raw MRT); omega_4 (BGK). */
 int lbm_strain(lbm_t h, double* out);
 int lbm_strain_device(lbm_t h, double* out);
 

@@ -424,11 +424,17 @@ void ONAME(oracle_macros)(const oracle_lattice* L, const real* f, real* rho, rea
 void ONAME(oracle_strain)(const oracle_lattice* L, const real* f, real* out)
 {
     const long plane = (long)L->nx * L->ny;
+    /* Eq. (28)-(30) divide by the rates at which the second-order moments relax:
+     * omega_3, omega_4, omega_5 for the cascaded and raw-MRT collisions, the
+     * single rate omega_4 for BGK. */
+    real om[6];
+    for (int k = 0; k < 6; ++k) om[k] = L->omega[k];
+    if (L->model == ORACLE_BGK) om[0] = om[2] = om[1];
     for (long n = 0; n < plane; ++n) {
         real fb[9], F[2], s[3];
         for (int a = 0; a < 9; ++a) fb[a] = f[a * plane + n];
         node_force(L, n, plane, F);
-        ONAME(oracle_strain_node)(fb, F, L->omega, s);
+        ONAME(oracle_strain_node)(fb, F, om, s);
         for (int k = 0; k < 3; ++k) out[k * plane + n] = s[k];
     }
 }

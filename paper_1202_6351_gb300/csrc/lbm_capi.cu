@@ -584,10 +584,19 @@ int lbm_macros(lbm_t h, double* rho, double* u) {
     return LBM_OK;
 }
 
+// Eq. (28)-(30) divide by the rates at which the second-order moments relax:
+// omega_3, omega_4, omega_5 for the cascaded and raw-MRT collisions, the single
+// rate omega_4 for BGK.
+static lbm::Args strain_args(const lbm_s* h) {
+    lbm::Args a = h->a;
+    if (h->model == LBM_BGK) a.om[0] = a.om[2] = a.om[1];
+    return a;
+}
+
 int lbm_strain_device(lbm_t h, double* out) {
     CHECK_HANDLE(h);
     if (!out) return fail(LBM_EINVAL, "out is NULL");
-    LBM_CUDA(lbm::launch_strain(h->a, h->store, h->t & 1, h->walls, force_mode(h), out, h->stream), "strain kernel");
+    LBM_CUDA(lbm::launch_strain(strain_args(h), h->store, h->t & 1, h->walls, force_mode(h), out, h->stream), "strain kernel");
     return LBM_OK;
 }
 
@@ -597,7 +606,7 @@ int lbm_strain(lbm_t h, double* out) {
     const size_t n = 3 * (size_t)nodes(h);
     DevBuf buf(h->stream);
     LBM_CUDA(buf.alloc(n * sizeof(double)), "strain staging");
-    LBM_CUDA(lbm::launch_strain(h->a, h->store, h->t & 1, h->walls, force_mode(h), static_cast<double*>(buf.p),
+    LBM_CUDA(lbm::launch_strain(strain_args(h), h->store, h->t & 1, h->walls, force_mode(h), static_cast<double*>(buf.p),
                                 h->stream),
              "strain kernel");
     LBM_CUDA(cudaMemcpyAsync(out, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "strain copy");

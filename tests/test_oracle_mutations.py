@@ -41,6 +41,10 @@ def _init():
     T.test_init_is_the_transformed_equilibrium(O.CASCADED)
 
 
+def _bgk_strain():
+    T.test_couette_moving_wall(O.BGK, "north")
+
+
 def _conservation():
     for m in (O.CASCADED, O.BGK, O.RAWMRT):
         T.test_collision_conserves_mass_and_adds_force(m)
@@ -52,7 +56,7 @@ def _corner_symmetry():
 
 def _strain_divergence():
     for om in ((1.3, 1.6, 1.6, 1.0, 1.0, 1.0), (1.6, 1.3, 1.3, 1.0, 1.0, 1.0)):
-        T.test_strain_divergence_satisfies_continuity(om)
+        T.test_strain_divergence_satisfies_continuity(O.CASCADED, om)
 
 
 def _force_field():
@@ -89,6 +93,8 @@ MUTATIONS = [
      "L->wall_u[wall];\n                        const real Uy = 0.0;", _couette_east),
     ("start state shifted by +S/2", "f[a * plane + n] = feq[a] - 0.5 * S[a];",
      "f[a * plane + n] = feq[a] + 0.5 * S[a];", _init),
+    ("BGK strain inverted with the cascaded rates", "if (L->model == ORACLE_BGK) om[0] = om[2] = om[1];",
+     "", _bgk_strain),
     ("bounce-back into the same direction", "const int b = OPP[a];", "const int b = a;", _streaming),
     ("lid term on the links through a corner", "if (!corner && L->edge[wall] == ORACLE_MOVING_WALL)",
      "if (L->edge[wall] == ORACLE_MOVING_WALL)", _corner_symmetry),

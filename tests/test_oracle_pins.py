@@ -468,11 +468,13 @@ def test_couette_moving_wall(model, wall):
     central moments about u, so u is; raw MRT relaxes raw moments towards
     equilibria of j = rho u, so j is, while rho varies across the channel at
     O(U^2) (u then deviates by about 1e-5 of U); BGK also keeps rho uniform.
-    Each of the four edges takes its turn as the moving wall."""
+    Each of the four edges takes its turn as the moving wall.  omega_4 !=
+    omega_5: the shear of Eq. 30 divides by omega_5, the rate of the xy moment,
+    for the cascaded and raw-MRT collisions and by omega_4 for BGK."""
     edges, speeds, along_x, far = COUETTE_WALLS[wall]
-    U, om, H = 0.05, 1.2, 16
+    U, H = 0.05, 16
     shape = (3, H) if along_x else (H, 3)
-    L = O.Lattice(*shape, (1, om, om, 1, 1, 1), edges=edges, wall_u=tuple(U * c for c in speeds),
+    L = O.Lattice(*shape, (1.0, 1.4, 1.2, 1.0, 1.0, 1.0), edges=edges, wall_u=tuple(U * c for c in speeds),
                   model=model)
     L.init().run(20000)
     rho, u = L.macros()
@@ -485,21 +487,23 @@ def test_couette_moving_wall(model, wall):
     if model == O.RAWMRT:
         assert 1e-6 < np.ptp(rho) < 1e-4
     shear = L.strain()[2]
-    np.testing.assert_allclose(shear, (1 if far else -1) * U / H, rtol=2e-2 if model == O.RAWMRT else 1e-6)
+    np.testing.assert_allclose(shear, (1 if far else -1) * U / H, rtol=1e-10)      # Eq. 30, omega_5
 
 
 @pytest.mark.parametrize("om", [(1.3, 1.6, 1.6, 1.0, 1.0, 1.0), (1.6, 1.3, 1.3, 1.0, 1.0, 1.0)])
-def test_strain_divergence_satisfies_continuity(om):
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_strain_divergence_satisfies_continuity(model, om):
     """Eq. 28 gives d_x j_x + d_y j_y from the bulk non-equilibrium moment with
-    omega_3.  Mass conservation fixes that sum independently: it equals
-    -d rho / dt.  A standing sound wave (rho = 1 + 1e-3 cos kx, at rest) has a
-    divergence, unlike the Taylor-Green and Couette flows; the moment-based
-    value must match the central time difference of rho to a few percent (with
-    omega_3 and omega_4 swapped it would be off by about 20 %)."""
+    the rate of that moment: omega_3 (cascaded, raw MRT), omega_4 (BGK).  Mass
+    conservation fixes that sum independently: it equals -d rho / dt.  A
+    standing sound wave (rho = 1 + 1e-3 cos kx, at rest) has a divergence,
+    unlike the Taylor-Green and Couette flows; the moment-based value must match
+    the central time difference of rho to a few percent (with omega_3 and
+    omega_4 swapped it would be off by about 20 %)."""
     nx, ny = 64, 4
     x = np.arange(nx)
     rho = np.tile(1 + 1e-3 * np.cos(2 * np.pi * x / nx), (ny, 1))
-    L = O.Lattice(nx, ny, om).init(rho, np.zeros((2, ny, nx)))
+    L = O.Lattice(nx, ny, om, model=model).init(rho, np.zeros((2, ny, nx)))
     L.run(9)
     r0, _ = L.macros()
     L.run(1)
