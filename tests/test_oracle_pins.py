@@ -571,12 +571,12 @@ def test_force_field_adds_to_the_uniform_force(model):
     assert np.abs(free - out[0]).max() > 1e-6
 
 
-def _tg_run(n, om=1.6, periods=1.0):
+def _tg_run(n, om=1.6, periods=1.0, model=O.CASCADED):
     nu = O.nu_from_omega(om)
     u0 = 0.04 * 64 / n
     steps = int(round(periods * O.taylor_green_decay_time(n, nu)))
     rho0, u_init, _ = O.taylor_green(n, u0, nu, 0)
-    L = O.Lattice(n, n, (1, om, om, 1, 1, 1)).init(rho0, u_init)
+    L = O.Lattice(n, n, (1, om, om, 1, 1, 1), model=model).init(rho0, u_init)
     L.run(steps)
     rho, u = L.macros()
     _, ua, sa = O.taylor_green(n, u0, nu, steps)
@@ -584,17 +584,27 @@ def _tg_run(n, om=1.6, periods=1.0):
     return O.relative_l2(u, ua), O.relative_l2(sxx, sa), O.relative_error_paper(u, ua)
 
 
-def test_taylor_green_second_order_convergence():
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_taylor_green_second_order_convergence(model):
     """Diffusive scaling U0 = 0.04*64/N, omega = 1.6, one decay time: errors in u
-    and in S_xx from non-equilibrium moments fall as N^-2 (Sec. III-B)."""
-    res = [_tg_run(n) for n in (16, 32, 64)]
+    and in S_xx from non-equilibrium moments fall as N^-2 (Sec. III-B), for the
+    cascaded collision and for both siblings.  BGK damps sound with the bulk
+    viscosity nu, a fifth of what omega_3 = 1 gives the others, so the standing
+    sound wave its start state emits along the Taylor-Green pressure modes
+    (wavelength N/2, period N sqrt(3)/2 steps) is still in its S_xx at one decay
+    time, with a phase that changes with N: there two doublings of N must cut
+    the S_xx error by more than 12x rather than each by 2^1.9."""
+    res = [_tg_run(n, model=model) for n in (16, 32, 64)]
     eu = np.array([r[0] for r in res])
     es = np.array([r[1] for r in res])
     su = np.log2(eu[:-1] / eu[1:])
     ss = np.log2(es[:-1] / es[1:])
     assert np.all((su > 1.9) & (su < 2.15)), su
-    assert np.all((ss > 1.9) & (ss < 2.15)), ss
-    assert res[-1][0] < 2e-3
+    if model == O.BGK:
+        assert es[0] / es[2] > 12, es
+    else:
+        assert np.all((ss > 1.9) & (ss < 2.15)), ss
+    assert res[-1][0] < 2e-3 and res[-1][1] < 1.5e-3
 
 
 def test_complex_step_build_matches_real_build_and_fd():
