@@ -2,7 +2,6 @@
 function, the primary and secondary vortex finders, the centre-line extraction
 and the strain-rate probes, checked on synthetic fields whose answers are known
 in closed form."""
-import math
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ Loss: L = 1/2 sum_x |u(x, T) - u_target(x)|^2 after T steps of a periodic
 cascaded lattice started at the transformed equilibrium with velocity u0.
 Gradients: dL/du0, dL/dF (per-node body force field), dL/domega_3..8.
 """
-import math
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ Bars: FP64 storage/arithmetic <= 1e-12 relative (max-norm of f) per step and
 steps; reduced-precision storage within the bounds stated in the test.
 Inputs are seeded; expected values come from the oracle only.
 """
-import math
 
 import numpy as np
 import pytest

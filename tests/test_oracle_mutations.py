@@ -7,12 +7,10 @@ library; the oracle module is pointed at it for the duration of one check.
 import os
 import subprocess
 
-import numpy as np
 import pytest
 
 import oracle as O
 from oracle import build as OB
-from tests import _pins as P
 from tests import test_oracle_pins as T
 
 
