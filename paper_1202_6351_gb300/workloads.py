@@ -31,7 +31,7 @@ def diffusive_u0(n: int, u_ref: float = 0.04, n_ref: int = 64) -> float:
 
 
 def random_fields(seed: int, nx: int, ny: int, u_amp: float = 0.05, rho_amp: float = 0.02):
-    """Smooth-free random (rho, u) fields for parity tests: rho = 1 + rho_amp*N(0,1),
+    """Uncorrelated random (rho, u) fields for parity tests: rho = 1 + rho_amp*N(0,1),
     u = u_amp*N(0,1) per node and component."""
     rng = np.random.default_rng(seed)
     rho = 1.0 + rho_amp * rng.standard_normal((ny, nx))
