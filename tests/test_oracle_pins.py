@@ -312,6 +312,49 @@ def cavity_centreline_errors(re=10.0, sides=(13, 19, 25, 37), reference=73, u_co
     return errs
 
 
+def _stagnation_point(u, guess):
+    """Zero of (u_x, u_y) near `guess` (in units of the side) from bicubic
+    interpolants of the node values; node i sits at x = (i + 1/2)/n between
+    half-way walls at 0 and 1."""
+    interp = pytest.importorskip("scipy.interpolate")
+    opt = pytest.importorskip("scipy.optimize")
+    n = u.shape[-1]
+    c = (np.arange(n) + 0.5) / n
+    sx = interp.RectBivariateSpline(c, c, u[0])        # indexed (y, x)
+    sy = interp.RectBivariateSpline(c, c, u[1])
+    sol = opt.fsolve(lambda p: [sx(p[1], p[0])[0, 0], sy(p[1], p[0])[0, 0]], guess, xtol=1e-12)
+    return sol
+
+
+def test_cavity_primary_vortex_at_re_100_matches_table_i():
+    """Sec. IV-C, Table I: the primary vortex of the lid-driven cavity at
+    Re = U (N - 1)/nu = 100 sits at (0.61482, 0.73543) (cascaded, 401^2 in the
+    paper).  The oracle on 65^2 (U = 0.1, steady to 1e-7 per 1000 steps) puts
+    the stagnation point u = v = 0 inside the vortex within 0.3 % of the side."""
+    n, U = 65, 0.1
+    nu = U * (n - 1) / 100.0
+    om = O.omega_from_nu(nu)
+    L = O.Lattice(n, n, (1, om, om, 1, 1, 1), edges=(O.BOUNCEBACK, O.BOUNCEBACK, O.BOUNCEBACK, O.MOVING_WALL),
+                  wall_u=(0, 0, 0, U)).init()
+    prev = None
+    for _ in range(100):
+        L.run(1000)
+        _, u = L.macros()
+        if prev is not None and np.abs(u - prev).max() < 1e-7:
+            break
+        prev = u
+    else:
+        pytest.fail("cavity did not reach a steady state")
+    speed = np.hypot(u[0], u[1])
+    core = speed[n // 2:7 * n // 8, n // 2:7 * n // 8]
+    j, i = np.unravel_index(np.argmin(core), core.shape)
+    guess = ((i + n // 2 + 0.5) / n, (j + n // 2 + 0.5) / n)
+    x, y = _stagnation_point(u, guess)
+    ref = P.PAPER["primary_vortex"]
+    expect = ref["cascaded"][ref["re"].index(100)]
+    assert abs(x - expect[0]) < 3e-3 and abs(y - expect[1]) < 3e-3, (x, y)
+
+
 @pytest.mark.slow
 def test_cavity_converges_at_second_order():
     """Sec. III-C finds second-order grid convergence of the centre-line
