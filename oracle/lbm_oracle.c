@@ -31,6 +31,8 @@
  *   - SRT-BGK and raw-moment MRT are only named by the paper; they are
  *     defined here with the second-order polynomial equilibrium and the same
  *     source S_a of Eq. (14).
+ *   - the strain rates of Eq. (28)-(30) divide by the rate at which each
+ *     non-equilibrium moment relaxes; under BGK that is omega_4 for all three.
  */
 #include <string.h>
 #include "lbm_oracle.h"
