@@ -3,11 +3,12 @@
 //
 // One thread per node (variant 0; variant 1 takes two rows per thread with
 // packed FP32x2 arithmetic, variant 2 four nodes of a row per thread with
-// 64-bit accesses for 16-bit stores): AA-pattern load of the nine populations (a1, a2),
-// decode to FP32/FP64 deviations (a3), macroscopic fields (a4, Eq. 26-27),
-// raw moments (a5, Eq. 15), source (a6, Eq. 13-14), cascaded kernel g3..g8
-// (a7, Eq. 17-22) or a sibling collision, back-transform (a8, Eq. 25), encode
-// and AA-pattern store (a9).  All of it in registers, one launch per time step.
+// 64-bit accesses for 16-bit stores): AA-pattern load of the nine populations
+// with the wall links resolved (Eq. 24, Sec. III-A, III-C), decode of the
+// stored deviations to FP32/FP64, macroscopic fields (Eq. 26-27), raw moments
+// (Eq. 15), source (Eq. 13-14), cascaded kernel g3..g8 (Eq. 17-22) or a
+// sibling collision, back-transform (Eq. 25), encode and AA-pattern store.
+// All of it in registers, one launch per time step.
 #pragma once
 
 #include "lbm_internal.h"
