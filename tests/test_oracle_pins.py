@@ -592,8 +592,9 @@ def test_init_is_the_transformed_equilibrium(model):
 @pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
 def test_force_field_adds_to_the_uniform_force(model):
     """A per-node force field equal to a constant F acts as the uniform force F,
-    and a field adds to the uniform force (reading 16): three ways of applying
-    the same total force give the same run."""
+    and a field adds to the uniform force of Eq. 5 (the paper has only the
+    uniform force; the per-node field is read as an addition to it): three ways
+    of applying the same total force give the same run."""
     nx, ny = 9, 7
     om = (1.2, 1.6, 1.5, 0.9, 1.1, 1.3)
     rng = np.random.default_rng(21)
