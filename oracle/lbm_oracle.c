@@ -9,8 +9,7 @@
  * first and streaming second, in the push form in which Eq. (23)-(24) are
  * written.  No blocking, fusion or reordering.
  *
- * Readings of the paper that this file takes (each is also listed in the
- * design notes):
+ * Readings of the paper that this file takes:
  *   - weights w_a (used in Sec. III-C but never printed) are the unique D2Q9
  *     populations whose central moments are (1,0,0,1/3,1/3,0,0,0,1/9) at u = 0,
  *     i.e. Eq. (10) with rho = 1: (4/9, 1/9 x4, 1/36 x4).

@@ -123,8 +123,9 @@ def test_taylor_green_strain_rate_converges_at_second_order_on_the_gpu():
 
 
 # Relative L2 velocity error at one decay time for 16-bit storage, as measured
-# (stated bounds with some margin): FP16 rounding stalls part of the slow viscous
-# decay, so the error grows with the number of steps (see the design notes).
+# (stated bounds with some margin): round to nearest drops every per-step change
+# below half a spacing of the stored type, which stalls part of the slow viscous
+# decay, so the error grows with the number of steps and is not monotone in N.
 ONE_DECAY_TIME_BOUNDS = {lbm.F16DEV: {64: 5e-3, 128: 1.5e-2, 256: 0.3, 1024: 6e-2},
                          lbm.BF16DEV: {64: 0.1, 128: 0.3, 256: 0.1, 1024: 0.7}}
 
