@@ -65,6 +65,12 @@ BAD_CREATE = [
     dict(edges=(lbm.PERIODIC, lbm.PERIODIC, lbm.MOVING_WALL, lbm.PERIODIC)),
     dict(edges=(5, 5, 0, 0)),
     dict(force=(float("nan"), 0.0)),
+    # size limits, one past each: ny <= 65535 (grid y dimension), and the row
+    # pitch (nx rounded up to 32) times ny within 2^31 - 1 (32-bit plane offsets)
+    dict(nx=8, ny=65536),
+    dict(nx=2147483, ny=1000),
+    dict(rho0=float("inf")),
+    dict(edges=(lbm.PERIODIC, lbm.PERIODIC, lbm.BOUNCEBACK, lbm.MOVING_WALL), wall_u=(0, 0, 0, float("inf"))),
 ]
 
 
@@ -76,6 +82,17 @@ def test_create_rejects_bad_arguments_before_touching_the_device(kw):
         lbm.lbm_create(**args)
     assert ei.value.code == lbm.LBM_EINVAL
     assert lbm.lbm_last_error()
+
+
+def test_largest_lattice_passes_the_argument_checks():
+    """32768 x 65535 (pitch 32768, 2^31 - 2^15 nodes per plane) is within every
+    size limit, so without a GPU lbm_create gets as far as looking for a device."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("would allocate the lattice")
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_create(32768, 65535, (1.0,) * 6, store=lbm.F16DEV)
+    assert ei.value.code == lbm.LBM_ECUDA
 
 
 def test_null_handles():
