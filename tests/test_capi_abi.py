@@ -95,6 +95,32 @@ def test_largest_lattice_passes_the_argument_checks():
     assert ei.value.code == lbm.LBM_ECUDA
 
 
+def _noalloc_layout(nx=8, ny=8, pitch=32, store=lbm.F32, rho0=1.0, edges=(0, 0, 0, 0)):
+    bc = lbm.lbm_bc_t((C.c_int * 4)(*edges), (C.c_double * 4)(0, 0, 0, 0))
+    return lbm.lbm_layout_t(nx, ny, pitch, store, 0, rho0, (C.c_double * 2)(0, 0), bc)
+
+
+BAD_NOALLOC = [
+    dict(nx=0), dict(ny=0), dict(ny=lbm.LBM_NOALLOC_MAX_ROWS + 1), dict(pitch=7),
+    dict(nx=131072, pitch=131072, ny=16384), dict(store=9), dict(rho0=0.0), dict(edges=(0, 0, 3, 0)),
+]
+
+
+@pytest.mark.parametrize("kw", BAD_NOALLOC)
+def test_noalloc_rejects_bad_layouts_before_touching_the_device(kw):
+    """lbm_stats_noalloc checks the caller's layout before any CUDA call, so a
+    rejected layout never reaches the (here dummy) buffers."""
+    lib = lbm.load_library()
+    dummy = C.c_double(0)
+    lay = _noalloc_layout(**kw)
+    rc = lib.lbm_stats_noalloc(C.addressof(dummy), C.byref(lay), C.addressof(dummy), None)
+    assert rc == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error().startswith("lbm_stats_noalloc")
+    for f, lp, out in ((None, C.byref(lay), C.addressof(dummy)), (C.addressof(dummy), None, C.addressof(dummy)),
+                       (C.addressof(dummy), C.byref(_noalloc_layout()), None)):
+        assert lib.lbm_stats_noalloc(f, lp, out, None) == lbm.LBM_EINVAL
+
+
 def test_null_handles():
     lib = lbm.load_library()
     assert lib.lbm_destroy(None) == lbm.LBM_OK
