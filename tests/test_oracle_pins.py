@@ -312,6 +312,31 @@ def cavity_centreline_errors(re=10.0, sides=(13, 19, 25, 37), reference=73, u_co
     return errs
 
 
+# x -> -x maps direction a to MIRROR_X[a] (e_x changes sign, e_y stays).
+MIRROR_X = [0, 3, 2, 1, 4, 6, 5, 8, 7]
+
+
+@pytest.mark.parametrize("model", [O.CASCADED, O.BGK, O.RAWMRT])
+def test_runs_are_equivariant_under_a_mirror_in_x(model):
+    """The lattice, all three collisions, the force along y and the west and
+    east walls moving alike along y are unchanged by x -> -x, so a start state
+    that is mirror-symmetric (rho and u_y even, u_x odd about the centre line)
+    stays so: f_a(x) = f_{a'}(nx - 1 - x) with a' the mirrored direction."""
+    nx, ny = 11, 9
+    rng = np.random.default_rng(31)
+    rho = 1 + 0.02 * rng.standard_normal((ny, nx))
+    u = 0.03 * rng.standard_normal((2, ny, nx))
+    rho = 0.5 * (rho + rho[:, ::-1])
+    u = np.stack([0.5 * (u[0] - u[0][:, ::-1]), 0.5 * (u[1] + u[1][:, ::-1])])
+    L = O.Lattice(nx, ny, (1.2, 1.6, 1.5, 0.9, 1.1, 1.3), force=(0.0, 2e-5),
+                  edges=(O.MOVING_WALL, O.MOVING_WALL, O.BOUNCEBACK, O.BOUNCEBACK),
+                  wall_u=(0.03, 0.03, 0.0, 0.0), model=model).init(rho, u).run(40)
+    f = L.f
+    mirrored = f[MIRROR_X][:, :, ::-1]
+    assert np.abs(f - f[:, :, ::-1]).max() > 1e-4      # not trivially symmetric
+    np.testing.assert_allclose(f, mirrored, rtol=0, atol=2e-15)     # a few ulps of f ~ 0.4
+
+
 def _stagnation_point(u, guess):
     """Zero of (u_x, u_y) near `guess` (in units of the side) from bicubic
     interpolants of the node values; node i sits at x = (i + 1/2)/n between
