@@ -456,6 +456,32 @@ def _channel_momentum(model, om, umax, steps, axis=0, H=32):
 SLIP_CASES = [((1.0, 0.7, 0.7, 1.5, 0.8, 1.0), 12000), ((1.2, 1.3, 0.7, 0.8, 1.6, 1.1), 40000)]
 
 
+def test_poiseuille_at_the_papers_configuration():
+    """Sec. IV-A: Re = U N / nu = 200, tau = 0.515 (the text; the figure caption
+    says 0.55), diffusive scaling over N = 26..401, maximum relative error
+    max |u - u_a| / U below 0.22 %.  The wall slip closed form gives that error
+    as 4 |2 Lambda - 1/4| / N^2 with Lambda = (tau - 1/2)(1/omega_7 - 1/2),
+    largest at the coarsest grid: N = 26 is run (from the parabola, eight decay
+    times of the slowest mode)."""
+    N, tau = 26, 0.515
+    om = 1 / tau
+    nu = O.nu_from_omega(om)
+    U = 200 * nu / N
+    fx = 8 * nu * U / N ** 2
+    y = np.arange(N) + 0.5
+    ua = 4 * U * y * (N - y) / N ** 2
+    u = np.zeros((2, N, 4))
+    u[0] = ua[:, None]
+    L = O.Lattice(4, N, (1, om, om, 1, 1, 1), force=(fx, 0),
+                  edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK)).init(np.ones((N, 4)), u)
+    L.run(int(8 * N ** 2 / (math.pi ** 2 * nu)))
+    _, v = L.macros()
+    err = np.abs(v[0][:, 0] - ua).max() / U
+    assert err < P.PAPER["poiseuille_max_rel_error"]["value"]
+    lam = (tau - 0.5) * (1 / 1.0 - 0.5)
+    assert err == pytest.approx(4 * abs(2 * lam - 0.25) / N ** 2, rel=1e-4)
+
+
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("om,steps", SLIP_CASES)
 @pytest.mark.parametrize("model", [O.BGK, O.RAWMRT])
