@@ -741,6 +741,34 @@ def test_taylor_green_second_order_convergence(model):
     assert res[-1][0] < 2e-3 and res[-1][1] < 1.5e-3
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("kk", [1, 2])
+def test_taylor_green_slopes_at_the_papers_configuration(kk):
+    """Sec. III-B's own study: tau = 0.55 for omega_4 = omega_5 (others 1),
+    k = 1 and 2 periods per box, u0 = 0.01 on 24^2 (Re = u0 N / nu = 14.4, the
+    box length being N nodes), diffusive scaling.  The paper fits slopes of
+    1.99 (k = 1) and 1.98 (k = 2) to the global error of u (Eq. 34) and of S_xx
+    over 24^2 .. 192^2; on 24^2, 48^2 and 96^2, at one decay time of the k = 1
+    mode, the oracle's mean slopes lie within 0.03 of those figures."""
+    om = 1 / 0.55
+    nu = O.nu_from_omega(om)
+    eu, es = [], []
+    for n in (24, 48, 96):
+        u0, k = 0.01 * 24 / n, 2 * math.pi * kk / n
+        steps = int(round(O.taylor_green_decay_time(n, nu)))
+        rho0, u_init, _ = O.taylor_green(n, u0, nu, 0, k=k)
+        L = O.Lattice(n, n, (1, om, om, 1, 1, 1)).init(rho0, u_init).run(steps)
+        rho, u = L.macros()
+        _, ua, sa = O.taylor_green(n, u0, nu, steps, k=k)
+        eu.append(O.relative_error_paper(u, ua))
+        es.append(O.relative_l2(L.strain()[0] / rho, sa))
+    su = np.log2(np.array(eu[:-1]) / np.array(eu[1:]))
+    ss = np.log2(np.array(es[:-1]) / np.array(es[1:]))
+    paper = P.PAPER["taylor_green_slopes"]
+    assert abs(su.mean() - paper["u"][kk - 1]) < 0.03, su
+    assert abs(ss.mean() - paper["sxx"][kk - 1]) < 0.03, ss
+
+
 def test_complex_step_build_matches_real_build_and_fd():
     """The complex build (used for complex-step gradients) agrees with the real
     build on real inputs, and its derivative matches central differences."""
