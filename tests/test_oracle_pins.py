@@ -482,6 +482,40 @@ def test_poiseuille_at_the_papers_configuration():
     assert err == pytest.approx(4 * abs(2 * lam - 0.25) / N ** 2, rel=1e-4)
 
 
+@pytest.mark.slow
+def test_poiseuille_convergence_study_of_the_paper():
+    """Sec. III-A: tau = 0.55 for omega_4 = omega_5 (others 1), channels of
+    3 x N nodes under diffusive scaling at Re = U N / nu = 100, 200, 400; the
+    global error of Eq. 34 falls with slope about 2.00 and grows slightly with
+    Re.  Here N = 24, 36, 48 (from the parabola, ten decay times of the slowest
+    mode): slopes within 0.02 of 2, errors increasing with Re at every N, and at
+    Re 100 the error of the wall slip closed form within 1 %."""
+    om = 1 / 0.55
+    nu = O.nu_from_omega(om)
+    lam = (0.55 - 0.5) * (1 / 1.0 - 0.5)
+    sides = (24, 36, 48)
+    errs = {}
+    for re in (100, 200, 400):
+        for N in sides:
+            U = re * nu / N
+            fx = 8 * nu * U / N ** 2
+            y = np.arange(N) + 0.5
+            ua = np.zeros((2, N, 3))
+            ua[0] = (4 * U * y * (N - y) / N ** 2)[:, None]
+            L = O.Lattice(3, N, (1, om, om, 1, 1, 1), force=(fx, 0),
+                          edges=(O.PERIODIC, O.PERIODIC, O.BOUNCEBACK, O.BOUNCEBACK)).init(np.ones((N, 3)), ua)
+            L.run(int(10 * N ** 2 / (math.pi ** 2 * nu)))
+            _, v = L.macros()
+            errs[re, N] = O.relative_error_paper(v, ua)
+            if re == 100:
+                slip = abs(2 * lam - 0.25) * 4 * U / N ** 2
+                assert errs[re, N] == pytest.approx(slip * N / ua[0][:, 0].sum(), rel=1e-2)
+        slope = math.log(errs[re, 24] / errs[re, 48]) / math.log(2)
+        assert abs(slope - 2) < 0.02, (re, slope)
+    for N in sides:
+        assert errs[100, N] < errs[200, N] < errs[400, N]
+
+
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("om,steps", SLIP_CASES)
 @pytest.mark.parametrize("model", [O.BGK, O.RAWMRT])
