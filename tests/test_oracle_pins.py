@@ -4,6 +4,7 @@ Nothing here compares the oracle with itself: each check uses the printed
 tables (tests/golden/), direct moment summation, conservation laws, closed-form
 flows (Poiseuille, Couette, Taylor-Green) or brute force on tiny lattices.
 """
+import functools
 import math
 
 import numpy as np
@@ -351,25 +352,31 @@ def _stagnation_point(u, guess):
     return sol
 
 
-def test_cavity_primary_vortex_at_re_100_matches_table_i():
-    """Sec. IV-C, Table I: the primary vortex of the lid-driven cavity at
-    Re = U (N - 1)/nu = 100 sits at (0.61482, 0.73543) (cascaded, 401^2 in the
-    paper).  The oracle on 65^2 (U = 0.1, steady to 1e-7 per 1000 steps) puts
-    the stagnation point u = v = 0 inside the vortex within 0.3 % of the side."""
+@functools.lru_cache(maxsize=1)
+def _cavity_re100_65():
+    """The lid-driven cavity at Re = U (N - 1)/nu = 100 on 65^2 (U = 0.1), run
+    until u changes by less than 1e-7 over 1000 steps: (rho, u, strain)."""
     n, U = 65, 0.1
-    nu = U * (n - 1) / 100.0
-    om = O.omega_from_nu(nu)
+    om = O.omega_from_nu(U * (n - 1) / 100.0)
     L = O.Lattice(n, n, (1, om, om, 1, 1, 1), edges=(O.BOUNCEBACK, O.BOUNCEBACK, O.BOUNCEBACK, O.MOVING_WALL),
                   wall_u=(0, 0, 0, U)).init()
     prev = None
     for _ in range(100):
         L.run(1000)
-        _, u = L.macros()
+        rho, u = L.macros()
         if prev is not None and np.abs(u - prev).max() < 1e-7:
-            break
+            return rho, u, L.strain()
         prev = u
-    else:
-        pytest.fail("cavity did not reach a steady state")
+    pytest.fail("cavity did not reach a steady state")
+
+
+def test_cavity_primary_vortex_at_re_100_matches_table_i():
+    """Sec. IV-C, Table I: the primary vortex of the lid-driven cavity at
+    Re 100 sits at (0.61482, 0.73543) (cascaded, 401^2 in the paper).  The
+    oracle on 65^2 puts the stagnation point u = v = 0 inside the vortex within
+    0.3 % of the side."""
+    _, u, _ = _cavity_re100_65()
+    n = u.shape[-1]
     speed = np.hypot(u[0], u[1])
     core = speed[n // 2:7 * n // 8, n // 2:7 * n // 8]
     j, i = np.unravel_index(np.argmin(core), core.shape)
@@ -378,6 +385,31 @@ def test_cavity_primary_vortex_at_re_100_matches_table_i():
     ref = P.PAPER["primary_vortex"]
     expect = ref["cascaded"][ref["re"].index(100)]
     assert abs(x - expect[0]) < 3e-3 and abs(y - expect[1]) < 3e-3, (x, y)
+
+
+# Probe points of Table III in units of the side.
+TABLE_III = {"A": (0.25, 0.5), "B": (0.5, 0.25), "C": (0.5, 0.5), "D": (0.5, 0.75), "E": (0.75, 0.5)}
+
+
+def test_cavity_strain_from_moments_matches_central_differences_table_iii():
+    """Sec. IV-C, Table III: at five points of the Re 100 cavity the strain rate
+    from the non-equilibrium moments (Eq. 29-30) agrees with second-order
+    central differences of u to within 2 % (the paper's finding; measured 1 % on
+    65^2), and each component has the sign Table III prints (its grid is not
+    stated, so its magnitudes are not comparable).  Each point takes the node
+    nearest to it; node i sits at (i + 1/2)/n."""
+    rho, u, strain = _cavity_re100_65()
+    n = u.shape[-1]
+    paper = P.PAPER["strain_rate_points"]["100"]
+    for name, (px, py) in TABLE_III.items():
+        i, j = int(round(px * n - 0.5)), int(round(py * n - 0.5))
+        dvdy_m, shear_m = strain[1, j, i] / rho[j, i], strain[2, j, i] / rho[j, i]
+        dvdy_fd = 0.5 * (u[1, j + 1, i] - u[1, j - 1, i])
+        shear_fd = 0.5 * (u[0, j + 1, i] - u[0, j - 1, i]) + 0.5 * (u[1, j, i + 1] - u[1, j, i - 1])
+        assert dvdy_m == pytest.approx(dvdy_fd, rel=0.02), name
+        assert shear_m == pytest.approx(shear_fd, rel=0.02), name
+        assert np.sign(dvdy_m) == np.sign(paper["dvdy"][name]), name
+        assert np.sign(shear_m) == np.sign(paper["shear"][name]), name
 
 
 @pytest.mark.slow
