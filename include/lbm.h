@@ -317,8 +317,11 @@ int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
  * threads) race on the array and must be serialised by the caller.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Allocates nothing.  Errors: LBM_EINVAL (NULL
- * pointer, sizes, pitch < nx, unknown store or edge kind), LBM_ECUDA. */
+ * before any stream capture.  The address is kept per device and looked up
+ * again by the first call after the device's context has been replaced (for
+ * example by cudaDeviceReset).  Allocates nothing.  Errors: LBM_EINVAL (NULL
+ * pointer, sizes, pitch < nx, unknown store or edge kind, one edge of an
+ * opposite pair periodic and the other a wall), LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_ROWS 16384
 
 typedef struct {

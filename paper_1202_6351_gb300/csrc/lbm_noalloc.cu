@@ -8,6 +8,8 @@
 // passes the population array and the output, and the per-row partial sums
 // live in a file-scope __device__ array of fixed size (kMaxRows rows), which
 // every GPU that loads this library holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "lbm.h"
@@ -26,19 +28,71 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_row_partials[3 * kMaxRows];
 
 std::mutex g_setup_mutex;
-double* g_partials_addr[kMaxDevices] = {};
 
-// Device address of g_row_partials on the current device (looked up once per
-// device; the symbol's host-side name is not a device address).
+// The device address of g_row_partials belongs to the CUDA context that loaded
+// this module: a device reset (cudaDeviceReset) destroys the primary context,
+// and the next one may place the array elsewhere.  The address is therefore
+// cached per device together with the id of the context it was looked up in,
+// and looked up again (once) whenever that id changes.
+struct PartialsCache {
+    unsigned long long ctx_id = 0;
+    double* addr = nullptr;
+};
+PartialsCache g_partials[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult(CUDAAPI*)(CUcontext*);
+using CtxGetIdFn = CUresult(CUDAAPI*)(CUcontext, unsigned long long*);
+
+// Id of the current context through the driver entry points (the library does
+// not link the driver library itself).
+cudaError_t current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return e != cudaSuccess ? e : cudaErrorUnknown;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return e != cudaSuccess ? e : cudaErrorUnknown;
+        get_id = reinterpret_cast<CtxGetIdFn>(p);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorUnknown;
+    return cudaSuccess;
+}
+
+// Device address of g_row_partials on the current device (the symbol's
+// host-side name is not a device address): looked up once per device, with
+// that device current, and again only after its context has been replaced.
 cudaError_t partials_address(int device, double** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[device]) {
+    PartialsCache& c = g_partials[device];
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e == cudaErrorDeviceUninitialized) {
+        // No context is current yet: the runtime makes the device's primary
+        // context current on its first call, here the lookup itself.
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_row_partials);
+        e = cudaGetSymbolAddress(&p, g_row_partials);
         if (e != cudaSuccess) return e;
-        g_partials_addr[device] = static_cast<double*>(p);
+        e = current_context_id(&id);
+        if (e != cudaSuccess) return e;
+        c.addr = static_cast<double*>(p);
+        c.ctx_id = id;
+    } else if (e != cudaSuccess) {
+        return e;
     }
-    *out = g_partials_addr[device];
+    if (c.ctx_id != id || !c.addr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_row_partials);
+        if (e != cudaSuccess) return e;
+        c.addr = static_cast<double*>(p);
+        c.ctx_id = id;
+    }
+    *out = c.addr;
     return cudaSuccess;
 }
 
@@ -82,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) row_sums_kernel(const Args a, bool o
     }
 }
 
-// Adds the row sums in row order (deterministic) into out[3].
+// Sums the row partials in a fixed order (deterministic) into out[3].
 __global__ void __launch_bounds__(kThreads) rows_finish_kernel(const double* partials, int ny, double* out) {
     __shared__ double sh[kThreads / 32];
     for (int k = 0; k < 3; ++k) {
@@ -108,6 +162,11 @@ extern "C" int lbm_stats_noalloc(const void* f, const lbm_layout_t* layout, doub
     if (!(L.rho0 > 0.0)) return fail(LBM_EINVAL, "rho0 must be positive");
     for (int k = 0; k < 4; ++k)
         if (L.bc.edge[k] < LBM_PERIODIC || L.bc.edge[k] > LBM_MOVING_WALL) return fail(LBM_EINVAL, "unknown edge kind");
+    // the pairing lbm_create enforces: opposite edges both periodic or both walls
+    if ((L.bc.edge[LBM_WEST] == LBM_PERIODIC) != (L.bc.edge[LBM_EAST] == LBM_PERIODIC))
+        return fail(LBM_EINVAL, "west and east edges must both be periodic or both be walls");
+    if ((L.bc.edge[LBM_SOUTH] == LBM_PERIODIC) != (L.bc.edge[LBM_NORTH] == LBM_PERIODIC))
+        return fail(LBM_EINVAL, "south and north edges must both be periodic or both be walls");
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)

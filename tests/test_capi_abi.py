@@ -103,6 +103,7 @@ def _noalloc_layout(nx=8, ny=8, pitch=32, store=lbm.F32, rho0=1.0, edges=(0, 0, 
 BAD_NOALLOC = [
     dict(nx=0), dict(ny=0), dict(ny=lbm.LBM_NOALLOC_MAX_ROWS + 1), dict(pitch=7),
     dict(nx=131072, pitch=131072, ny=16384), dict(store=9), dict(rho0=0.0), dict(edges=(0, 0, 3, 0)),
+    dict(edges=(0, 1, 0, 0)), dict(edges=(0, 0, 2, 0)),  # one edge of an opposite pair periodic, the other a wall
 ]
 
 

@@ -28,7 +28,7 @@ def _layout(L, edges, wall_u, force, rho0=1.0):
     return lay, info["state"]
 
 
-@pytest.mark.parametrize("store", [lbm.F32, lbm.F64, lbm.F16DEV], ids=["f32", "f64", "f16"])
+@pytest.mark.parametrize("store", [lbm.F32, lbm.F64, lbm.BF16DEV, lbm.F16DEV], ids=["f32", "f64", "bf16", "f16"])
 def test_noalloc_stats_match_lbm_stats_on_two_calls(store):
     import torch
 
@@ -57,6 +57,15 @@ def test_noalloc_stats_match_lbm_stats_on_two_calls(store):
     lay, state = _layout(L, edges, wall_u, force)
     assert lib.lbm_stats_noalloc(state, C.byref(lay), out.data_ptr(), stream) == lbm.LBM_OK
     torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL, atol=1e-12)
+    # The entry point's contract: after the first call (which looks up the
+    # scratch address and may load the module's kernels), further calls leave
+    # the device's free memory unchanged.
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(20):
+        assert lib.lbm_stats_noalloc(state, C.byref(lay), out.data_ptr(), stream) == lbm.LBM_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL, atol=1e-12)
     L.close()
 
