@@ -11,6 +11,10 @@
   the lid speed on a fixed coarse grid at fixed viscosity (Sec. V).
 * :func:`secondary_vortex` locates the corner vortices of Table II and
   :func:`cavity_convergence` runs the grid-convergence study of Sec. III-C.
+* :func:`cavity_matrix` runs the lid-driven cavity at several Reynolds numbers
+  with the three collision models side by side, each in FP32 storage (to a
+  steady state) and in FP16 storage with both rounding modes (for the same
+  number of steps), one batched launch per model and step.
 
 All lattice work goes through the C ABI (:mod:`paper_1202_6351_gb300.lbm`);
 this module only sets parameters and post-processes fields with numpy.
@@ -277,3 +281,162 @@ def cavity_convergence(sides=(13, 19, 25, 31, 37, 49), reference=121, re=100.0, 
             errs[k] = float(np.sqrt(((q[k] - qi) ** 2).sum() / (qi ** 2).sum()))
         out[n] = errs
     return out
+
+
+# ---------------------------------------------------------------------------
+# The cavity configuration: Re x model x storage side by side
+
+
+def _blown_up(u):
+    return not np.isfinite(u).all() or float(np.abs(u).max()) > 1.0
+
+
+def cavity_matrix(n, res=(1000.0, 3200.0, 5000.0), models=(lbm.CASCADED, lbm.BGK, lbm.RAWMRT), U=0.1, tol=1e-7,
+                  check=1000, max_steps=20_000_000, f16=True, seed=2026, progress=None):
+    """Lid-driven cavities of n x n nodes at each Reynolds number in `res`
+    (nu = U (n - 1) / Re, other rates 1, from rest; Sec. IV-C, V) for each
+    collision model, each in FP32 storage and, if `f16`, in FP16 storage with
+    round to nearest and with stochastic rounding.  All lattices of one model
+    advance together in one batched launch per step (lbm.Batch); the batches of
+    the models run on their own streams at the same time.
+
+    A case (model, Re) runs until its FP32 lattice is steady (max |u(t) -
+    u(t - check)| < tol) or blows up (a non-finite velocity or |u| > 1), or
+    until max_steps.  Its FP16 lattices run the same number of steps and are
+    compared with the FP32 field then (FP16 storage resolves velocities only to
+    about 1e-5, so it has no steady state at tol; with stochastic rounding its
+    field keeps a random jitter).
+
+    Returns {(model, re): {"steps", "status" ("steady", "diverged" or
+    "unsteady"), "f32": {...}, "f16_nearest": {...}, "f16_stochastic": {...}}};
+    each storage entry holds the velocity field "u", its "max_du" over the last
+    `check` steps and, when finite, the primary vortex "centre" and the
+    secondary vortices of Table II; the FP16 entries also hold "rel_l2_vs_f32"
+    (relative L2 difference of the velocity from the FP32 field) and
+    "centre_shift" (distance of the primary vortex from the FP32 one)."""
+    om_other = 1.0
+    cases = {}
+    for model in models:
+        for re in res:
+            om = cavity_omega(n, re, U)
+            rates = (om_other, om, om, om_other, om_other, om_other)
+            kinds = [("f32", lbm.F32, None)]
+            if f16:
+                kinds += [("f16_nearest", lbm.F16DEV, lbm.ROUND_NEAREST),
+                          ("f16_stochastic", lbm.F16DEV, lbm.ROUND_STOCHASTIC)]
+            lat = {}
+            for name, st, rounding in kinds:
+                L = lbm.Lattice(n, n, rates, edges=CAVITY_EDGES, wall_u=(0, 0, 0, U), model=model, store=st)
+                if rounding == lbm.ROUND_STOCHASTIC:
+                    L.set_rounding(rounding, seed)
+                L.init()
+                lat[name] = L
+            cases[model, float(re)] = {"lattices": lat, "prev": {}, "result": None}
+
+    def batches():
+        out = []
+        for model in models:
+            ls = [L for (m, _), c in cases.items() if m == model and c["result"] is None for L in c["lattices"].values()]
+            if ls:
+                out.append(lbm.Batch(ls))
+        return out
+
+    live = batches()
+    steps = 0
+    try:
+        while live and steps < max_steps:
+            for B in live:
+                B.step(check)
+            for B in live:
+                B.sync()
+            steps += check
+            changed = False
+            for key, c in cases.items():
+                if c["result"] is not None:
+                    continue
+                fields = {name: L.macros()[1] for name, L in c["lattices"].items()}
+                u32 = fields["f32"]
+                du = {name: (float(np.abs(u - c["prev"][name]).max()) if name in c["prev"] else float("inf"))
+                      for name, u in fields.items()}
+                status = None
+                if _blown_up(u32):
+                    status = "diverged"
+                elif du["f32"] < tol:
+                    status = "steady"
+                elif steps >= max_steps:
+                    status = "unsteady"
+                if status is not None:
+                    c["result"] = _matrix_entry(status, steps, fields, du)
+                    changed = True
+                    if progress:
+                        progress(key, c["result"])
+                c["prev"] = fields
+            if changed:
+                for B in live:
+                    B.close()
+                live = batches()
+    finally:
+        for B in live:
+            B.close()
+        for c in cases.values():
+            for L in c["lattices"].values():
+                L.close()
+    out = {}
+    for key, c in cases.items():
+        out[key] = c["result"] if c["result"] is not None else {"steps": steps, "status": "unsteady"}
+    return out
+
+
+def _matrix_entry(status, steps, fields, du):
+    entry = {"steps": steps, "status": status}
+    u32 = fields["f32"]
+    c32 = None
+    for name, u in fields.items():
+        e = {"u": u, "max_du": du[name]}
+        if not _blown_up(u):
+            e["centre"] = vortex_centre(u)
+            e["secondary"] = {r: secondary_vortex(u, r) for r in SECONDARY_REGIONS}
+            if name == "f32":
+                c32 = e["centre"]
+            elif c32 is not None:
+                e["rel_l2_vs_f32"] = float(np.sqrt(((u - u32) ** 2).sum() / (u32 ** 2).sum()))
+                e["centre_shift"] = float(math.hypot(e["centre"][0] - c32[0], e["centre"][1] - c32[1]))
+        entry[name] = e
+    return entry
+
+
+def matrix_summary(results):
+    """The cavity matrix without velocity fields, keyed "model/Re" (JSON-ready)."""
+    out = {}
+    for (model, re), r in sorted(results.items()):
+        row = {"steps": r["steps"], "status": r["status"]}
+        for name in ("f32", "f16_nearest", "f16_stochastic"):
+            if name in r:
+                row[name] = {k: v for k, v in r[name].items() if k != "u"}
+        out[f"{lbm.MODEL_NAMES[model]}/{int(re)}"] = row
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import time
+
+    ap = argparse.ArgumentParser(description="Run the lid-driven cavity matrix (three models, FP32 / FP16) on the GPU.")
+    ap.add_argument("--n", type=int, default=257)
+    ap.add_argument("--re", type=float, nargs="+", default=[1000.0, 3200.0, 5000.0])
+    ap.add_argument("--models", nargs="+", default=["cascaded", "bgk", "rawmrt"])
+    ap.add_argument("--max-steps", type=int, default=20_000_000)
+    ap.add_argument("--no-f16", action="store_true")
+    args = ap.parse_args()
+    names = {v: k for k, v in lbm.MODEL_NAMES.items()}
+    t0 = time.time()
+
+    def report(key, r):
+        print(json.dumps({"case": f"{lbm.MODEL_NAMES[key[0]]}/{int(key[1])}", "n": args.n,
+                          "seconds": round(time.time() - t0, 1),
+                          **matrix_summary({key: r})[f"{lbm.MODEL_NAMES[key[0]]}/{int(key[1])}"]}), flush=True)
+
+    res = cavity_matrix(args.n, tuple(args.re), tuple(names[m] for m in args.models), max_steps=args.max_steps,
+                        f16=not args.no_f16, progress=report)
+    print(json.dumps({"n": args.n, "seconds": round(time.time() - t0, 1), "matrix": matrix_summary(res)}), flush=True)

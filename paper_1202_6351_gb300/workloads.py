@@ -25,6 +25,23 @@ def taylor_green_init(n: int, u0: float, rho0: float = 1.0):
     return rho, np.stack([ux, uy])
 
 
+def taylor_green_velocity(n: int, u0: float, nu: float, t: float):
+    """The analytic Taylor-Green velocity of Sec. III-B at time t on the n x n
+    node grid of taylor_green_init: the initial field times exp(-2 nu k^2 t),
+    k = 2 pi / n.  Returns u[2, n, n] (float64).  This is the decaying solution
+    of the Navier-Stokes equations the lattice results are compared with, not
+    lattice Boltzmann arithmetic."""
+    _, u = taylor_green_init(n, u0)
+    k = 2.0 * math.pi / n
+    return u * math.exp(-2.0 * nu * k * k * t)
+
+
+def taylor_green_decay_steps(n: int, nu: float) -> int:
+    """One decay time T = 1 / (2 nu k^2), k = 2 pi / n (Sec. III-B), rounded to whole steps."""
+    k = 2.0 * math.pi / n
+    return int(round(1.0 / (2.0 * nu * k * k)))
+
+
 def diffusive_u0(n: int, u_ref: float = 0.04, n_ref: int = 64) -> float:
     """Diffusive scaling of Sec. III (Ma/Kn constant): U0 = u_ref * n_ref / n."""
     return u_ref * n_ref / n

@@ -51,3 +51,28 @@ def test_whole_job_value_counts_every_rank():
     assert bench.whole_job_mlups(1000, 10, 1.0, 1) == pytest.approx(0.01)
     assert bench.whole_job_mlups(1000, 10, 1.0, 4) == pytest.approx(0.04)
     assert bench.max_over_ranks(2.5) == 2.5
+
+
+def test_digest_ignores_comments_and_layout_but_not_code():
+    code = "int f(int a) {\n  return a + 1; // add one\n}\n/* block\n comment */\n"
+    assert bench.strip_comments(code) == bench.strip_comments("int f(int a)   { return a + 1; }")
+    assert bench.strip_comments(code) != bench.strip_comments("int f(int a) { return a + 2; }")
+
+
+def test_timed_passes_span_the_minimum_window():
+    assert bench.passes_for(1.0) == bench.MIN_PASSES
+    assert bench.passes_for(0.004) * 0.004 >= bench.MIN_TIMED_SECONDS
+    assert bench.passes_for(10.0) == bench.MIN_PASSES
+
+
+def test_adjoint_bytes_count_forward_recompute_and_reverse():
+    # 2 steps, one checkpoint every 2: forward 2 x 80, recompute 1 x 80, reverse 2 x 132 per node
+    assert bench.adjoint_bytes_per_run(1, 2, 2) == 2 * 80 + 80 + 2 * 132
+    # a checkpoint every step: nothing is recomputed
+    assert bench.adjoint_bytes_per_run(4, 10, 1) == 16 * (10 * 80 + 10 * 132)
+
+
+def test_both_arms_describe_the_same_workload():
+    c = bench.workload_config(4096, "f32")
+    assert c["workload"] == "taylor_green_4096x4096_cascaded_f32_store" and c["nodes"] == 4096 ** 2
+    assert [k for k, _ in bench.CPU_SAMPLES].count("cavity") == 1
