@@ -124,21 +124,24 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * variant outside 0..2. */
 int lbm_set_variant(lbm_t h, int variant);
 
-/* Rounding of the stored 16-bit deviations (LBM_BF16DEV, LBM_F16DEV).
+/* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
  * LBM_ROUND_NEAREST (the default) rounds to nearest even.  LBM_ROUND_STOCHASTIC
  * rounds each stored value up with probability equal to its distance above the
  * representable value below, in units of their spacing, so that the stored
  * state is an unbiased estimate of the computed one.  Round to nearest loses
  * every per-step change smaller than half a spacing; over long runs this stalls
  * the slow viscous decay (a Taylor-Green vortex on 256^2 in FP16 ends one decay
- * time 22 % too strong), which stochastic rounding removes.  The random bits
- * come from a counter-based hash of (seed, step, node, population): a run is
- * reproducible for a given seed, independent of kernel variant, CTA shape and
- * CUDA-graph replay (variant 1 runs variant 0 in this mode).  Costs extra
- * integer instructions per stored value.
- * LBM_EINVAL for another mode or for stochastic rounding with FP32/FP64
- * storage.  Batches (lbm_batch_*) round each lattice as it is set here, with
- * the same results as lbm_step. */
+ * time 22 % too strong), which stochastic rounding removes.  For FP32 storage
+ * the computed value is known exactly: the last addition of the collision
+ * (Eq. 25) is an error-free sum (TwoSum), and its remainder is rounded in.
+ * The random bits come from a counter-based hash of (seed, step, node,
+ * population): a run is reproducible for a given seed, independent of kernel
+ * variant, CTA shape and CUDA-graph replay (variant 1 runs variant 0 in this
+ * mode).  Costs extra integer and FP32 instructions per stored value.
+ * LBM_EINVAL for another mode or for stochastic rounding with FP64 storage.
+ * Batches (lbm_batch_*) round each lattice as it is set here, with the same
+ * results as lbm_step; lbm_adjoint_run recomputes the rounded forward states
+ * and differentiates the rounding as the identity. */
 #define LBM_ROUND_NEAREST 0
 #define LBM_ROUND_STOCHASTIC 1
 int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);

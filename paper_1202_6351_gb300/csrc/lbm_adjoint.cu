@@ -185,6 +185,19 @@ __global__ void __launch_bounds__(kThreads) adj_fold_kernel(long long count, con
     if (i < count) gF[i] += double(gs[i]);
 }
 
+// The launch arguments of forward step t: with stochastic rounding of the
+// stores, the hash of (seed, t), so that the recomputed states are bit for bit
+// the forward ones (the reverse pass treats the rounding as the identity).
+Args at_step(const Args& a, long t) {
+    Args ak = a;
+    if (ak.rseed) {
+        ak.rbase = round_hash(ak.rseed, static_cast<unsigned long long>(t));
+        ak.rtable = nullptr;
+        ak.tstep = 0;
+    }
+    return ak;
+}
+
 template <int ST>
 cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, const double* u0, const double* target,
                         char* ckpt, char* seg, void* lam0, void* lam1, double* gF, float* gseg, double* acc,
@@ -205,7 +218,8 @@ cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, co
         if ((e = cudaMemcpyAsync(ckpt + c * SB, h->state, SB, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
         const long len = std::min(every, nsteps - c * every);
         for (long k = 0; k < len; ++k) {
-            if ((e = launch_step_any(a, h->store, h->model, h->t & 1, fm, false, s)) != cudaSuccess) return e;
+            if ((e = launch_step_any(at_step(a, h->t), h->store, h->model, h->t & 1, fm, false, s)) != cudaSuccess)
+                return e;
             ++h->t;
         }
     }
@@ -221,7 +235,7 @@ cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, co
         for (long k = 1; k < len; ++k) {
             if ((e = cudaMemcpyAsync(seg + k * SB, seg + (k - 1) * SB, SB, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
                 return e;
-            Args ak = a;
+            Args ak = at_step(a, n0 + k - 1);
             ak.f = seg + k * SB;
             if ((e = launch_step_any(ak, h->store, h->model, (n0 + k - 1) & 1, fm, false, s)) != cudaSuccess) return e;
         }

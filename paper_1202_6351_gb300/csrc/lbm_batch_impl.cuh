@@ -41,7 +41,10 @@ __device__ __forceinline__ void batch_node_store(const BatchDomain& D, int x, in
 template <int MODEL, bool ODD>
 __device__ __forceinline__ void batch_node(const BatchDomain& D, int x, int y, unsigned rb) {
     switch (D.store) {
-        case LBM_F32: batch_node_store<MODEL, LBM_F32, ODD, false>(D, x, y, 0u); break;
+        case LBM_F32:
+            if (D.a.rseed) batch_node_store<MODEL, LBM_F32, ODD, true>(D, x, y, rb);
+            else batch_node_store<MODEL, LBM_F32, ODD, false>(D, x, y, 0u);
+            break;
         case LBM_F16DEV:
             if (D.a.rseed) batch_node_store<MODEL, LBM_F16DEV, ODD, true>(D, x, y, rb);
             else batch_node_store<MODEL, LBM_F16DEV, ODD, false>(D, x, y, 0u);

@@ -377,8 +377,8 @@ int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed) {
     CHECK_HANDLE(h);
     if (mode != LBM_ROUND_NEAREST && mode != LBM_ROUND_STOCHASTIC)
         return fail(LBM_EINVAL, "rounding mode must be LBM_ROUND_NEAREST or LBM_ROUND_STOCHASTIC");
-    if (mode == LBM_ROUND_STOCHASTIC && h->store != LBM_F16DEV && h->store != LBM_BF16DEV)
-        return fail(LBM_EINVAL, "stochastic rounding applies to LBM_BF16DEV and LBM_F16DEV storage");
+    if (mode == LBM_ROUND_STOCHASTIC && h->store == LBM_F64)
+        return fail(LBM_EINVAL, "stochastic rounding applies to LBM_F32, LBM_BF16DEV and LBM_F16DEV storage");
     // rseed != 0 selects stochastic rounding; mix the caller's seed into a nonzero word
     h->a.rseed = mode == LBM_ROUND_STOCHASTIC ? ((seed ^ 0x2545f4914f6cdd1dULL) | 1ULL) : 0ULL;
     h->a.rtable = nullptr;

@@ -23,7 +23,10 @@
 // (Sec. III-C); a diagonal link through the corner point of two walls is
 // reflected without it (see incoming_wall).
 // The 16-bit stores round to nearest even or, per lattice, stochastically
-// (StochasticRound, random offsets from a counter-based hash).
+// (StochasticRound, random offsets from a counter-based hash).  FP32 stores
+// can round stochastically too: the collision then forms the last addition of
+// Eq. (25) as an error-free sum (two_sum) and the store rounds its exact
+// remainder in (round_sr32).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -102,6 +105,40 @@ __device__ __forceinline__ typename Store<STORE>::T enc_sr(typename Store<STORE>
     if constexpr (STORE == LBM_F16DEV) return __ushort_as_half(StochasticRound<STORE>::enc(v, r));
     else if constexpr (STORE == LBM_BF16DEV) return __ushort_as_bfloat16(StochasticRound<STORE>::enc(v, r));
     else return Store<STORE>::enc(v);
+}
+
+// Error-free sum (Knuth's TwoSum): s = fl(a + b) and err with a + b = s + err
+// exactly, for round-to-nearest FP32 without overflow.  The intrinsics keep
+// the compiler from contracting or reassociating the operations.
+LBM_HD float two_sum(float a, float b, float& err) {
+#ifdef __CUDA_ARCH__
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+#else
+    volatile float vs = a + b;
+    const float s = vs;
+    volatile float vbb = s - a;
+    const float bb = vbb;
+    err = (a - (s - bb)) + (b - bb);
+#endif
+    return s;
+}
+
+// Stochastic rounding of an FP32 value known exactly as s + e (s = fl(s + e)):
+// s moves to its neighbour on the side of e with probability |e| / gap, gap
+// the distance to that neighbour, so the stored value is an unbiased estimate
+// of s + e.  r is a uniform random 32-bit word; its top 24 bits give
+// u = k 2^-24 and u * gap is exact (gap is a power of two).  s = 0 implies
+// e = 0 (a sum that rounds to zero is exact with gradual underflow), so the
+// neighbour of +-0 is never taken.
+__device__ __forceinline__ float round_sr32(float s, float e, unsigned r) {
+    const unsigned bits = __float_as_uint(s);
+    const bool away = (e > 0.f) == (s > 0.f);  // magnitude grows
+    const float nb = __uint_as_float(away ? bits + 1u : bits - 1u);
+    const float gap = fabsf(nb - s);
+    const float u = __uint2float_rz(r >> 8) * 0x1p-24f;
+    return fabsf(e) > u * gap ? nb : s;
 }
 
 // ---------------------------------------------------------------- launch arguments
@@ -272,16 +309,24 @@ __device__ __forceinline__ unsigned round_node(const Args& a, unsigned base, int
 
 // Store the nine post-collision deviations of node (x, y).
 // rb: the hash C0 of this launch's (seed, step) when SR (stochastic rounding).
+// For FP32 storage with SR, err[q] is the exact remainder of d[q] (the
+// collision's two_sum), which round_sr32 rounds in.
 template <int STORE, bool ODD, bool WALLS, bool SR = false>
 __device__ __forceinline__ void store_node(const Args& a, int x, int y, const typename Store<STORE>::R d[9],
-                                           unsigned rb) {
+                                           unsigned rb, const typename Store<STORE>::R* err = nullptr) {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
+    constexpr bool SR32 = SR && STORE == LBM_F32;
     T* __restrict__ f = static_cast<T*>(a.f);
     const int n = y * a.pitch + x;
     const unsigned rn = SR ? round_node(a, rb, x, y) : 0u;
-    auto enc = [&](R v, int q) -> T { return SR ? enc_sr<STORE>(v, rn + static_cast<unsigned>(q) * kRoundStride) : S::enc(v); };
+    auto put = [&](R v, R e, int q) -> T {
+        const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+        if constexpr (SR32) return round_sr32(v, e, r);
+        else return SR ? enc_sr<STORE>(v, r) : S::enc(v);
+    };
+    auto enc = [&](R v, int q) -> T { return put(v, SR32 ? err[q] : R(0), q); };
     if (!ODD) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) plane_ptr(a, f, opp(q))[n] = enc(d[q], q);
@@ -294,7 +339,13 @@ __device__ __forceinline__ void store_node(const Args& a, int x, int y, const ty
             int w = -1;
             if (WALLS) w = incoming_wall(a, opp(q), x, y);
             if (w >= 0) {
-                plane_ptr(a, f, opp(q))[n] = enc(d[q] + wall_term<R>(a, opp(q), w), q);
+                if constexpr (SR32) {
+                    float e2;
+                    const float v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
+                    plane_ptr(a, f, opp(q))[n] = put(v, err[q] + e2, q);
+                } else {
+                    plane_ptr(a, f, opp(q))[n] = enc(d[q] + wall_term<R>(a, opp(q), w), q);
+                }
             } else {
                 const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);
                 const int tr = cy(q) == 1 ? rp : (cy(q) == -1 ? rm : r0);
@@ -397,10 +448,39 @@ LBM_HD void add_kernel(R d[9], R g3, R g4, R g5, R g6, R g7, R g8) {
     d[8] += t - p - g7;
 }
 
+// The increments K . g of add_kernel as separate values (the error-free path).
+template <typename R>
+LBM_HD void kernel_increments(R inc[9], R g3, R g4, R g5, R g6, R g7, R g8) {
+    const R t = R(2) * g3 + g8;
+    const R a = g4 - g3, b = -g3 - g4;
+    const R p = g5 - g6, q = g5 + g6;
+    inc[0] = R(4) * (g8 - g3);
+    inc[1] = a + R(2) * (g7 - g8);
+    inc[3] = a - R(2) * (g7 + g8);
+    inc[2] = b + R(2) * (g6 - g8);
+    inc[4] = b - R(2) * (g6 + g8);
+    inc[5] = t + p - g7;
+    inc[6] = t - q + g7;
+    inc[7] = t + q + g7;
+    inc[8] = t - p - g7;
+}
+
+// d += inc, with each sum's exact remainder in err when TS (FP32 only).
+template <typename R, bool TS>
+LBM_HD void add_increments(R d[9], const R inc[9], R* err) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        if constexpr (TS) d[q] = two_sum(d[q], inc[q], err[q]);
+        else d[q] += inc[q];
+    }
+}
+
 // ---------------------------------------------------------------- cascaded collision
 // Sec. II, Eq. (13)-(25), on deviations.  FORCE = 0: no source terms.
-template <typename R, bool FORCED>
-LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
+// TS (FP32 with stochastic rounding of the store): the post-collision value
+// d + (K g + S) is formed by one error-free sum whose remainder goes to err.
+template <typename R, bool FORCED, bool TS = false>
+LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (27)
@@ -430,6 +510,18 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
                          + R(2) * (ux * m.kxyy + uy * m.kxxy) - uxx * kyy_t - uyy * kxx_t
                          - R(4) * uxy * m.kxy - R(0.5) * sxxyy)
                - R(2) * g3 - R(0.5) * (uyy * A + uxx * B) - R(4) * uxy * g5 - R(2) * (uy * g6 + ux * g7);
+    if constexpr (TS) {
+        R inc[9];
+        kernel_increments(inc, g3, g4, g5, g6, g7, g8);
+        if (FORCED) {
+            R S[9];
+            source(ux, uy, Fx, Fy, S);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) inc[q] += S[q];
+        }
+        add_increments<R, true>(d, inc, err);
+        return;
+    }
     add_kernel(d, g3, g4, g5, g6, g7, g8);
     if (FORCED) {
         R S[9];
@@ -441,8 +533,8 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c) {
 
 // ---------------------------------------------------------------- SRT-BGK sibling
 // d~ = d - w (d - d_eq) + (1 - w/2) S with the 2nd-order polynomial f_eq and w = omega_4.
-template <typename R, bool FORCED>
-LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
+template <typename R, bool FORCED, bool TS = false>
+LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
@@ -455,16 +547,22 @@ LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c) {
     for (int q = 0; q < 9; ++q) {
         const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
         const R deq = wgt<R>(q) * (m.drho + m.rho * (R(3) * eu + R(4.5) * eu * eu - usq));
-        d[q] = d[q] - w * (d[q] - deq);
-        if (FORCED) d[q] += (R(1) - R(0.5) * w) * S[q];
+        if constexpr (TS) {
+            R inc = -w * (d[q] - deq);
+            if (FORCED) inc += (R(1) - R(0.5) * w) * S[q];
+            d[q] = two_sum(d[q], inc, err[q]);
+        } else {
+            d[q] = d[q] - w * (d[q] - deq);
+            if (FORCED) d[q] += (R(1) - R(0.5) * w) * S[q];
+        }
     }
 }
 
 // ---------------------------------------------------------------- raw-moment MRT sibling
 // f~ = f - K D^-1 [L (m - m_eq) - (I - L/2) m_s], L = diag(0,0,0,omega_3..omega_8),
 // basis K of Eq. (3), polynomial equilibrium moments m_eq in closed form.
-template <typename R, bool FORCED>
-LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
+template <typename R, bool FORCED, bool TS = false>
+LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) {
     const Moments<R> m = moments(d, c.rho0);
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
@@ -502,6 +600,20 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
     // d += K g over b = 3..8 with columns of Eq. (3), plus the momentum source F/6 on K1, K2
     R fx6 = 0, fy6 = 0;
     if (FORCED) { fx6 = Fx * R(1.0 / 6.0); fy6 = Fy * R(1.0 / 6.0); }
+    if constexpr (TS) {
+        R inc[9];
+        inc[0] = R(-4) * g3 + R(4) * g8;
+        inc[1] = fx6 - g3 + g4 + R(2) * g7 - R(2) * g8;
+        inc[2] = fy6 - g3 - g4 + R(2) * g6 - R(2) * g8;
+        inc[3] = -fx6 - g3 + g4 - R(2) * g7 - R(2) * g8;
+        inc[4] = -fy6 - g3 - g4 - R(2) * g6 - R(2) * g8;
+        inc[5] = fx6 + fy6 + R(2) * g3 + g5 - g6 - g7 + g8;
+        inc[6] = -fx6 + fy6 + R(2) * g3 - g5 - g6 + g7 + g8;
+        inc[7] = -fx6 - fy6 + R(2) * g3 + g5 + g6 + g7 + g8;
+        inc[8] = fx6 - fy6 + R(2) * g3 - g5 + g6 - g7 + g8;
+        add_increments<R, true>(d, inc, err);
+        return;
+    }
     d[0] += R(-4) * g3 + R(4) * g8;
     d[1] += fx6 - g3 + g4 + R(2) * g7 - R(2) * g8;
     d[2] += fy6 - g3 - g4 + R(2) * g6 - R(2) * g8;
@@ -513,25 +625,28 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c) {
     d[8] += fx6 - fy6 + R(2) * g3 - g5 + g6 - g7 + g8;
 }
 
-template <int MODEL, typename R, bool FORCED>
-LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c) {
-    if (MODEL == LBM_CASCADED) collide_cascaded<R, FORCED>(d, Fx, Fy, c);
-    else if (MODEL == LBM_BGK) collide_bgk<R, FORCED>(d, Fx, Fy, c);
-    else collide_rawmrt<R, FORCED>(d, Fx, Fy, c);
+template <int MODEL, typename R, bool FORCED, bool TS = false>
+LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) {
+    if (MODEL == LBM_CASCADED) collide_cascaded<R, FORCED, TS>(d, Fx, Fy, c, err);
+    else if (MODEL == LBM_BGK) collide_bgk<R, FORCED, TS>(d, Fx, Fy, c, err);
+    else collide_rawmrt<R, FORCED, TS>(d, Fx, Fy, c, err);
 }
 
 // ---------------------------------------------------------------- one node, one step
 // a1-a9: AA-pattern load, decode, force, collision, encode, AA-pattern store.
+// With SR on FP32 storage the collision keeps the exact remainder of each
+// post-collision value for the stochastic rounding of the store.
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false>
 __device__ __forceinline__ void step_node(const Args& a, int x, int y, unsigned rb) {
     using R = typename Store<STORE>::R;
+    constexpr bool TS = SR && STORE == LBM_F32;
     const Coef<R> c(a);
-    R d[9];
+    R d[9], err[9];
     load_node<STORE, ODD, WALLS>(a, x, y, d);
     R Fx, Fy;
     node_force<R, FORCE>(a, x, y, Fx, Fy);
-    collide<MODEL, R, (FORCE != 0)>(d, Fx, Fy, c);
-    store_node<STORE, ODD, WALLS, SR>(a, x, y, d, rb);
+    collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, err);
+    store_node<STORE, ODD, WALLS, SR>(a, x, y, d, rb, err);
 }
 
 // As step_node; with walls, only nodes on the lattice edge take the wall-aware

@@ -85,6 +85,14 @@ static cudaError_t launch_vec(const Args& a, cudaStream_t s) {
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
+    if constexpr (STORE == LBM_F32) {
+        if (a.rseed) {  // stochastic rounding of FP32 stores: variant 0 only
+            const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
+            const dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
+            step_kernel<MODEL, STORE, ODD, FORCE, WALLS, true><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (STORE == LBM_F16DEV || STORE == LBM_BF16DEV) {
         if (a.rseed) {  // stochastic rounding: variants 0 and 2 (variant 1 runs variant 0)
             if constexpr (FORCE != 2) {

@@ -52,8 +52,9 @@ def make(spec, seed):
 
 
 def with_rounding(L, i):
-    """Stochastic rounding on the 16-bit lattices except domain 3 (seed = index)."""
-    if L.store in (lbm.F16DEV, lbm.BF16DEV) and i != 3:
+    """Stochastic rounding on the 16-bit lattices except domain 3 and on the
+    FP32 lattices 4 and 5 (seed = index)."""
+    if (L.store in (lbm.F16DEV, lbm.BF16DEV) and i != 3) or i in (4, 5):
         L.set_rounding(lbm.ROUND_STOCHASTIC, i)
     return L
 

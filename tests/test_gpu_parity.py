@@ -448,9 +448,9 @@ def test_init_and_macros_read_and_write_pinned_host_buffers_in_place(store):
     np.testing.assert_array_equal(results[1][2], results[1][3])
 
 
-# ---------------------------------------------------------------- stochastic rounding of 16-bit stores
+# ---------------------------------------------------------------- stochastic rounding of the stores
 
-@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV], ids=["f16", "bf16"])
+@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV, lbm.F32], ids=["f16", "bf16", "f32"])
 @pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
 @pytest.mark.parametrize("edges,force", [("periodic", (0.0, 0.0)), ("cavity", (0.0, 0.0)),
                                          ("channel", (2e-5, 1e-5))])
@@ -475,7 +475,9 @@ def test_stochastic_rounding_is_the_same_in_every_variant_and_graph_length(store
         return out
 
     ref = run(0, 0, 7)
-    for variant, graph_steps in ((2, 0), (0, 8), (2, 8), (2, 64)):
+    # FP32 storage has variants 0 and 1 (variant 1 runs variant 0 in this mode)
+    others = ((1, 0), (0, 8), (1, 8), (0, 64)) if store == lbm.F32 else ((2, 0), (0, 8), (2, 8), (2, 64))
+    for variant, graph_steps in others:
         for k, (a, b) in enumerate(zip(run(variant, graph_steps, 7), ref)):
             np.testing.assert_array_equal(a, b, err_msg=f"variant {variant}, graph {graph_steps}, chunk {k}")
     other = run(0, 0, 8)
@@ -485,10 +487,11 @@ def test_stochastic_rounding_is_the_same_in_every_variant_and_graph_length(store
     f_rn = nearest.get_f()
     nearest.close()
     assert not np.array_equal(f_rn, ref[-1])
-    assert np.abs(ref[-1] - f_rn).max() <= 1e-3  # the same flow, rounded differently
+    # the same flow, rounded differently
+    assert np.abs(ref[-1] - f_rn).max() <= (1e-3 if store != lbm.F32 else 1e-6)
 
 
-@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV], ids=["f16", "bf16"])
+@pytest.mark.parametrize("store", [lbm.F16DEV, lbm.BF16DEV, lbm.F32], ids=["f16", "bf16", "f32"])
 def test_stochastic_rounding_keeps_mass_and_rejects_misuse(store):
     n = 128
     rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
@@ -496,16 +499,46 @@ def test_stochastic_rounding_keeps_mass_and_rejects_misuse(store):
     m0 = g.stats()[0]
     g.step(1000)
     m1 = g.stats()[0]
-    assert abs(m1 - m0) / m0 <= (2e-6 if store == lbm.F16DEV else 2e-5)
+    assert abs(m1 - m0) / m0 <= {lbm.F16DEV: 2e-6, lbm.BF16DEV: 2e-5, lbm.F32: 1e-10}[store]
     with pytest.raises(lbm.LBMError):
         g.set_rounding(5)
     g.set_rounding(lbm.ROUND_NEAREST)
     g.close()
-    f32 = lbm.Lattice(16, 16, OMEGAS, store=lbm.F32)
+    f64 = lbm.Lattice(16, 16, OMEGAS, store=lbm.F64)
     with pytest.raises(lbm.LBMError):
-        f32.set_rounding(lbm.ROUND_STOCHASTIC, 1)
-    f32.set_rounding(lbm.ROUND_NEAREST)
-    f32.close()
+        f64.set_rounding(lbm.ROUND_STOCHASTIC, 1)
+    f64.set_rounding(lbm.ROUND_NEAREST)
+    f64.close()
+
+
+def test_fp32_stochastic_rounding_removes_the_storage_drift():
+    """Taylor-Green on 4096^2 (the bench workload, U0 = 6.25e-4): the viscous
+    change of a stored deviation per step is only a few FP32 units in the last
+    place, and round to nearest loses part of it every step, so the decay drifts
+    away from the analytic one.  With the collision's last addition formed as an
+    error-free sum and its remainder rounded in stochastically the stored state
+    is unbiased.  After T/50 = 101,993 steps (Sec. III-B: T = 1 / (2 nu k^2)) the
+    stochastic run is within 2e-7 of the analytic decay in amplitude (the
+    discretisation error at this size is about 2e-7 in velocity, relative L2), the
+    round-to-nearest run is not."""
+    n = 4096
+    om = OMEGAS[1]
+    nu = (1.0 / om - 0.5) / 3.0
+    u0 = workloads.diffusive_u0(n)
+    steps = workloads.taylor_green_decay_steps(n, nu) // 50
+    rho, u = workloads.taylor_green_init(n, u0)
+    ua = workloads.taylor_green_velocity(n, u0, nu, steps)
+    res = {}
+    for mode in (lbm.ROUND_NEAREST, lbm.ROUND_STOCHASTIC):
+        with lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), store=lbm.F32) as g:
+            g.set_rounding(mode, 11).init(rho, u).step(steps)
+            _, ug = g.macros()
+        res[mode] = (float(np.sqrt(((ug - ua) ** 2).sum() / (ua ** 2).sum())), float((ug * ua).sum() / (ua * ua).sum()))
+        print("FP32", "stochastic" if mode else "nearest", steps, "steps: u error %.3e, amplitude %.8f" % res[mode])
+    err_sr, amp_sr = res[lbm.ROUND_STOCHASTIC]
+    err_rn, amp_rn = res[lbm.ROUND_NEAREST]
+    assert abs(amp_sr - 1.0) < 2e-7 and err_sr < 1e-6
+    assert abs(amp_rn - 1.0) > 5 * abs(amp_sr - 1.0)
 
 
 def test_tune_keeps_state_and_picks_a_variant():
