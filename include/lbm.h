@@ -244,10 +244,14 @@ size_t lbm_bytes_per_update(int store);
  * Accumulation over time of dL/domega is FP64; dL/dF is summed in the
  * arithmetic type over the steps of one checkpoint segment and in FP64 across
  * segments (FP64 throughout for LBM_F64).  Requirements: the cascaded model,
- * LBM_F64 or LBM_F32 storage, four periodic edges.  Device memory used during
- * the call: (ceil(nsteps/every) + min(every, nsteps)) times the population
- * array, two adjoint arrays, a segment force-gradient array (FP32 storage) and
- * small scratch, allocated and released in stream order.  Synchronous.
+ * LBM_F64 or LBM_F32 storage, four periodic edges.  The forward pass writes
+ * each checkpoint directly (the step into a checkpoint runs out of place) and
+ * the recomputed states of a segment are stepped out of place from it, so no
+ * state is copied; every = 1 keeps every state and recomputes nothing.
+ * Device memory used during the call: (ceil(nsteps/every) +
+ * max(1, min(every, nsteps) - 1)) times the population array, two adjoint
+ * arrays, a segment force-gradient array (FP32 storage) and small scratch,
+ * allocated and released in stream order.  Synchronous.
  * Leaves the lattice at step nsteps. */
 int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const double* u0, const double* u_target,
                     double* loss, double* grad_u0, double* grad_force, double grad_omega[6]);

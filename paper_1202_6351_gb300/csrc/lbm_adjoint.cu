@@ -94,45 +94,54 @@ __global__ void __launch_bounds__(kThreads) adj_final_kernel(const Args a, bool 
 // on the first reverse step of a checkpoint segment (`first`), added after
 // that; adj_fold_kernel adds each segment's sum into the FP64 gradient (for
 // FP64 storage gs is the FP64 gradient itself and `first` is false).
+// Each thread takes kAdjRows node rows (y0, y0 + 1, ...) of its column and
+// sums their rate adjoints in registers, so the block reduction of the six
+// sums runs once per kAdjRows nodes.
+constexpr int kAdjRows = 4;
+
 template <int ST>
-__global__ void __launch_bounds__(kThreads) adj_step_kernel(const Args a, bool odd, int force,
+__global__ void __launch_bounds__(kThreads, ST == LBM_F32 ? 4 : 1) adj_step_kernel(const Args a, bool odd, int force,
                                                             const typename Store<ST>::R* __restrict__ lin,
                                                             typename Store<ST>::R* __restrict__ lout,
                                                             typename Store<ST>::R* __restrict__ gs, bool first,
                                                             double* gc) {
     using R = typename Store<ST>::R;
-    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    const int x = blockIdx.x * kThreads + threadIdx.x, y0 = blockIdx.y * kAdjRows;
     R c[6] = {0, 0, 0, 0, 0, 0};
     if (x < a.nx) {
-        R d[9];
-        load_rt<ST>(a, odd, x, y, d);
-        R Fx, Fy;
-        force_rt<R>(a, force, x, y, Fx, Fy);
         const int xm = x > 0 ? x - 1 : a.nx - 1, xp = x < a.nx - 1 ? x + 1 : 0;
-        const int rm = (y > 0 ? y - 1 : a.ny - 1) * a.pitch, rp = (y < a.ny - 1 ? y + 1 : 0) * a.pitch;
-        const int r0 = y * a.pitch;
-        R mu[9];
+        const int yend = min(y0 + kAdjRows, a.ny);
+#pragma unroll 1
+        for (int y = y0; y < yend; ++y) {
+            const Coef<R> co(a);
+            R d[9];
+            load_rt<ST>(a, odd, x, y, d);
+            R Fx, Fy;
+            force_rt<R>(a, force, x, y, Fx, Fy);
+            const int rm = (y > 0 ? y - 1 : a.ny - 1) * a.pitch, rp = (y < a.ny - 1 ? y + 1 : 0) * a.pitch;
+            const int r0 = y * a.pitch;
+            R mu[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {  // mu_q(x) = lambda_q(x + e_q)
-            const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);
-            const int tr = cy(q) == 1 ? rp : (cy(q) == -1 ? rm : r0);
-            mu[q] = lin[q * a.plane + tr + tx];
+            for (int q = 0; q < 9; ++q) {  // mu_q(x) = lambda_q(x + e_q)
+                const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);
+                const int tr = cy(q) == 1 ? rp : (cy(q) == -1 ? rm : r0);
+                mu[q] = lin[q * a.plane + tr + tx];
+            }
+            CollideAdjoint<R> g;
+            collide_cascaded_vjp<R>(d, Fx, Fy, co, mu, g);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) lout[q * a.plane + r0 + x] = g.d[q];
+            const int n = y * a.nx + x, p = a.nx * a.ny;
+            if (first) {
+                gs[n] = g.Fx;
+                gs[p + n] = g.Fy;
+            } else {
+                gs[n] += g.Fx;
+                gs[p + n] += g.Fy;
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) c[k] += g.c[k];
         }
-        const Coef<R> co(a);
-        CollideAdjoint<R> g;
-        collide_cascaded_vjp<R>(d, Fx, Fy, co, mu, g);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) lout[q * a.plane + r0 + x] = g.d[q];
-        const int n = y * a.nx + x, p = a.nx * a.ny;
-        if (first) {
-            gs[n] = g.Fx;
-            gs[p + n] = g.Fy;
-        } else {
-            gs[n] += g.Fx;
-            gs[p + n] += g.Fy;
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) c[k] = g.c[k];
     }
     block_atomic_add<6>(c, gc);
 }
@@ -211,40 +220,50 @@ cudaError_t run_reverse(lbm_s* h, long nsteps, long every, const double* rho, co
     const long nck = (nsteps + every - 1) / every;
     cudaError_t e;
 
-    // forward pass with checkpoints
-    if ((e = launch_init(a, h->store, h->model, fm, rho, u0, s)) != cudaSuccess) return e;
+    // Forward pass.  f^t lives in ckpt[c] at the checkpoint times t = c every and
+    // in the lattice's own array otherwise (and at t = nsteps); a step whose
+    // input and output live in different arrays runs out of place (Args::fo),
+    // the others in place, so no state is ever copied.
+    auto where = [&](long t) -> char* {
+        return (t % every == 0 && t < nsteps) ? ckpt + (t / every) * SB : static_cast<char*>(h->state);
+    };
+    {
+        Args a0 = a;
+        a0.f = ckpt;
+        if ((e = launch_init(a0, h->store, h->model, fm, rho, u0, s)) != cudaSuccess) return e;
+    }
     h->t = 0;
-    for (long c = 0; c < nck; ++c) {
-        if ((e = cudaMemcpyAsync(ckpt + c * SB, h->state, SB, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-        const long len = std::min(every, nsteps - c * every);
-        for (long k = 0; k < len; ++k) {
-            if ((e = launch_step_any(at_step(a, h->t), h->store, h->model, h->t & 1, fm, false, s)) != cudaSuccess)
-                return e;
-            ++h->t;
-        }
+    for (long t = 0; t < nsteps; ++t) {
+        Args ak = at_step(a, t);
+        ak.f = where(t);
+        char* out = where(t + 1);
+        ak.fo = out != ak.f ? out : nullptr;
+        if ((e = launch_step_any(ak, h->store, h->model, t & 1, fm, false, s)) != cudaSuccess) return e;
+        ++h->t;
     }
     R* cur = static_cast<R*>(lam0);
     R* nxt = static_cast<R*>(lam1);
     adj_final_kernel<ST><<<grid, kThreads, 0, s>>>(a, nsteps & 1, fm, target, cur, gF, acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    // reverse sweep, one recomputed segment at a time
+    // Reverse sweep, one segment at a time: f^{n0} is read from its checkpoint
+    // and f^{n0 + k}, k = 1 .. len - 1, recomputed out of place into seg slot k - 1.
     for (long c = nck - 1; c >= 0; --c) {
         const long n0 = c * every, len = std::min(every, nsteps - n0);
-        if ((e = cudaMemcpyAsync(seg, ckpt + c * SB, SB, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        auto state = [&](long k) -> char* { return k == 0 ? ckpt + c * SB : seg + (k - 1) * SB; };
         for (long k = 1; k < len; ++k) {
-            if ((e = cudaMemcpyAsync(seg + k * SB, seg + (k - 1) * SB, SB, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-                return e;
             Args ak = at_step(a, n0 + k - 1);
-            ak.f = seg + k * SB;
+            ak.f = state(k - 1);
+            ak.fo = state(k);
             if ((e = launch_step_any(ak, h->store, h->model, (n0 + k - 1) & 1, fm, false, s)) != cudaSuccess) return e;
         }
         R* gs = ST == LBM_F64 ? reinterpret_cast<R*>(gF) : reinterpret_cast<R*>(gseg);
+        const dim3 agrid(grid.x, (a.ny + kAdjRows - 1) / kAdjRows);
         for (long k = len - 1; k >= 0; --k) {
             Args ak = a;
-            ak.f = seg + k * SB;
+            ak.f = state(k);
             const bool first = ST != LBM_F64 && k == len - 1;
-            adj_step_kernel<ST><<<grid, kThreads, 0, s>>>(ak, (n0 + k) & 1, fm, cur, nxt, gs, first, acc + 1);
+            adj_step_kernel<ST><<<agrid, kThreads, 0, s>>>(ak, (n0 + k) & 1, fm, cur, nxt, gs, first, acc + 1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             std::swap(cur, nxt);
         }
@@ -293,7 +312,7 @@ extern "C" int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* r
         bufs.clear();
     };
     char* ckpt = static_cast<char*>(alloc(nck * SB));
-    char* seg = static_cast<char*>(alloc(seglen * SB));
+    char* seg = static_cast<char*>(alloc(std::max(1L, seglen - 1) * SB));
     void* lam0 = alloc(lam_bytes);
     void* lam1 = alloc(lam_bytes);
     double* acc = static_cast<double*>(alloc(7 * sizeof(double)));
@@ -304,7 +323,7 @@ extern "C" int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* r
         cudaGetLastError();
         if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
         return set_error(LBM_ENOMEM, "lbm_adjoint_run: cannot allocate %.1f MB of checkpoints and buffers",
-                         ((nck + seglen) * SB + 2 * lam_bytes) / 1e6);
+                         ((nck + std::max(1L, seglen - 1)) * SB + 2 * lam_bytes) / 1e6);
     }
     cudaError_t e = cudaMemsetAsync(acc, 0, 7 * sizeof(double), s);
     if (e == cudaSuccess) {

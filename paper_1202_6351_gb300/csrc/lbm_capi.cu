@@ -123,7 +123,8 @@ struct DevBuf {
 
 // True if two argument blocks launch the same step kernels on the same data.
 bool same_launch(const Args& x, const Args& y) {
-    if (x.f != y.f || x.plane != y.plane || x.nx != y.nx || x.ny != y.ny || x.pitch != y.pitch) return false;
+    if (x.f != y.f || x.fo != y.fo || x.plane != y.plane || x.nx != y.nx || x.ny != y.ny || x.pitch != y.pitch)
+        return false;
     if (x.ffield != y.ffield || x.variant != y.variant || x.block_x != y.block_x || x.scale != y.scale) return false;
     if (x.rseed != y.rseed) return false;
     for (int k = 0; k < 4; ++k)

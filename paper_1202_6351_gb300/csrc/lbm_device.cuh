@@ -151,6 +151,10 @@ enum : int { kCorner = 4 };
 
 struct Args {
     void* f;                  // populations [9][ny][pitch] of the stored type
+    void* fo;                 // where the one-node kernels store the step's result; null: f (in place).
+                              // Every slot is read and written by one thread, so a step from f into a
+                              // second array of the same layout needs no other change (the adjoint
+                              // recomputes its checkpoint segments this way instead of copying)
     long long plane;          // pitch * ny
     int nx, ny, pitch;
     int wall[4];              // 1 if the edge (W, E, S, N) is a wall
@@ -318,7 +322,7 @@ __device__ __forceinline__ void store_node(const Args& a, int x, int y, const ty
     using T = typename S::T;
     using R = typename S::R;
     constexpr bool SR32 = SR && STORE == LBM_F32;
-    T* __restrict__ f = static_cast<T*>(a.f);
+    T* __restrict__ f = static_cast<T*>(a.fo ? a.fo : a.f);
     const int n = y * a.pitch + x;
     const unsigned rn = SR ? round_node(a, rb, x, y) : 0u;
     auto put = [&](R v, R e, int q) -> T {

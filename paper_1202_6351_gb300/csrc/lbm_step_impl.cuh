@@ -96,15 +96,15 @@ static cudaError_t launch_one(const Args& a, cudaStream_t s) {
     if constexpr (STORE == LBM_F16DEV || STORE == LBM_BF16DEV) {
         if (a.rseed) {  // stochastic rounding: variants 0 and 2 (variant 1 runs variant 0)
             if constexpr (FORCE != 2) {
-                if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, true>(a, s);
+                if (a.variant == 2 && !a.fo) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, true>(a, s);
             }
             const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
             const dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
             step_kernel<MODEL, STORE, ODD, FORCE, WALLS, true><<<grid, block, 0, s>>>(a);
             return cudaGetLastError();
         }
-        if constexpr (FORCE != 2) {
-            if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, false>(a, s);
+        if constexpr (FORCE != 2) {  // the four-node kernel steps in place only
+            if (a.variant == 2 && !a.fo) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, false>(a, s);
         }
     }
     const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
