@@ -115,13 +115,21 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * four consecutive nodes of a row per thread, each population plane moved
  * with 64-bit accesses, elements at vector edges exchanged between
  * neighbouring lanes, and the per-node path where a neighbour wraps or a wall
- * is near.  The default is 2 for 16-bit stores of at least 2^20 nodes and 0
+ * is near; 3 (LBM_F32, LBM_BF16DEV, LBM_F16DEV) = two time steps per launch
+ * (temporal blocking): a CTA loads a 64 x 16 tile with a two-node halo by one
+ * TMA copy into shared memory, takes both steps there and writes the tile
+ * once, so the populations cross HBM once per two steps.  Variant 3 keeps a
+ * second population array (ping-pong, allocated by this call; LBM_ENOMEM if
+ * it does not fit), runs pairs of steps from even steps and single steps
+ * (variant 2 for 16-bit stores, else 0) otherwise, needs a lattice of at
+ * least 4 x 4 nodes and is not used while the divergence check is on.
+ * The default is 2 for 16-bit stores of at least 2^20 nodes and 0
  * otherwise (a smaller launch is latency-bound and one node per thread is
  * faster).
- * Variants 0 and 2 produce bit-identical states; variant 1 may round
+ * Variants 0, 2 and 3 produce bit-identical states; variant 1 may round
  * differently in the last bit because it fuses multiply-adds explicitly.
  * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
- * variant outside 0..2. */
+ * variant outside 0..3; a variant the storage kind does not admit selects 0. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
@@ -147,11 +155,12 @@ int lbm_set_variant(lbm_t h, int variant);
 int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
- * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads) on
- * the lattice itself (the state is snapshot and restored, so it is left
- * unchanged) and keeps the fastest pair; ms (may be NULL) receives the best
- * time per step of variants 0..2 (0 where not run).  Synchronous. */
-int lbm_tune(lbm_t h, int trial_steps, float ms[3]);
+ * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads;
+ * variant 3 has one fixed tile) on the lattice itself (the state is snapshot
+ * and restored, so it is left unchanged) and keeps the fastest pair; ms (may
+ * be NULL) receives the best time per step of variants 0..3 (0 where not run).
+ * Synchronous. */
+int lbm_tune(lbm_t h, int trial_steps, float ms[4]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own

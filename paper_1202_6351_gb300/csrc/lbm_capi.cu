@@ -11,6 +11,7 @@
 #include <string>
 
 #include "lbm.h"
+#include "lbm_fused.cuh"
 #include "lbm_internal.h"
 #include "lbm_handle.h"
 
@@ -95,14 +96,150 @@ size_t elem_size(int store) {
 
 using lbm::force_mode;
 
-cudaError_t launch_step(lbm_s* h, bool odd) {
+// The single-step variant that stands in for variant 3 (two fused steps) where
+// one step is taken alone: four nodes per thread for 16-bit stores, else one.
+int single_variant(const lbm_s* h) {
+    if (h->a.variant != 3) return h->a.variant;
+    return (h->store == LBM_F16DEV || h->store == LBM_BF16DEV) ? 2 : 0;
+}
+
+cudaError_t launch_step_at(lbm_s* h, bool odd, long t) {
     if (h->a.rseed) {  // stochastic rounding: the hash of (seed, step) of this launch
-        h->a.rbase = lbm::round_hash(h->a.rseed, static_cast<unsigned long long>(h->t));
+        h->a.rbase = lbm::round_hash(h->a.rseed, static_cast<unsigned long long>(t));
         h->a.rtable = nullptr;
         h->a.tstep = 0;
     }
-    return lbm::launch_step_any(h->a, h->store, h->model, odd, force_mode(h), h->walls, h->stream);
+    lbm::Args a = h->a;
+    a.variant = single_variant(h);
+    return lbm::launch_step_any(a, h->store, h->model, odd, force_mode(h), h->walls, h->stream);
 }
+
+cudaError_t launch_step(lbm_s* h, bool odd) { return launch_step_at(h, odd, h->t); }
+
+// ---------------------------------------------------------------- two fused steps (variant 3)
+
+using EncodeTiledFn = CUresult(CUDAAPI*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                         CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                         CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// does not link the driver library itself).
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+template <int ST>
+void fused_box(cuuint32_t box[3]) {
+    box[0] = lbm::FusedGeom<ST>::BW;
+    box[1] = lbm::FusedGeom<ST>::BH;
+    box[2] = 9;
+}
+
+// TMA descriptor of a population array of the lattice: a 3-D tensor
+// [9][ny][nx] (x fastest, row pitch `pitch`, plane pitch * ny), box = the
+// fused kernel's region; coordinates beyond nx or ny read zeros.
+cudaError_t encode_map(const lbm_s* h, void* base, CUtensorMap* map) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const size_t es = elem_size(h->store);
+    const cuuint64_t dims[3] = {cuuint64_t(h->a.nx), cuuint64_t(h->a.ny), 9};
+    const cuuint64_t strides[2] = {cuuint64_t(h->a.pitch) * es, cuuint64_t(h->a.plane) * es};
+    cuuint32_t box[3];
+    CUtensorMapDataType type;
+    if (h->store == LBM_F32) {
+        fused_box<LBM_F32>(box);
+        type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    } else {
+        fused_box<LBM_F16DEV>(box);
+        type = CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    }
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The fused kernel runs on FP32 and 16-bit storage, lattices of at least 4 x 4
+// nodes and without the divergence check (which needs the state every step).
+bool fused_active(const lbm_s* h) {
+    return h->a.variant == 3 && h->store != LBM_F64 && h->a.nx >= 4 && h->a.ny >= 4 && h->check_every == 0;
+}
+
+// Second population array, descriptors and error word (first use of variant 3).
+cudaError_t ensure_fused(lbm_s* h) {
+    cudaError_t e = cudaSuccess;
+    if (!h->state_alt) e = cudaMalloc(&h->state_alt, h->state_bytes);
+    if (e == cudaSuccess && !h->d_err) {
+        e = cudaMalloc((void**)&h->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    }
+    // The two arrays only ever swap roles, so one descriptor each, made once.
+    if (e == cudaSuccess && !h->tmap_ptr[0]) {
+        e = encode_map(h, h->state, &h->tmap[0]);
+        if (e == cudaSuccess) e = encode_map(h, h->state_alt, &h->tmap[1]);
+        if (e == cudaSuccess) {
+            h->tmap_ptr[0] = h->state;
+            h->tmap_ptr[1] = h->state_alt;
+        }
+    }
+    return e;
+}
+
+const CUtensorMap& map_of(const lbm_s* h, const void* base) { return h->tmap[h->tmap_ptr[0] == base ? 0 : 1]; }
+
+// Two steps from a.f (natural layout, t even) into `out`, the other array.
+cudaError_t launch_fused(lbm_s* h, const lbm::Args& a, void* out, cudaStream_t s) {
+    const CUtensorMap& map = map_of(h, a.f);
+    switch (h->store) {
+        case LBM_F32: return lbm::launch_fused_f32(map, a, out, h->d_err, h->model, force_mode(h), h->walls, s);
+        case LBM_BF16DEV: return lbm::launch_fused_bf16(map, a, out, h->d_err, h->model, force_mode(h), h->walls, s);
+        default: return lbm::launch_fused_f16(map, a, out, h->d_err, h->model, force_mode(h), h->walls, s);
+    }
+}
+
+void swap_arrays(lbm_s* h) {
+    std::swap(h->state, h->state_alt);
+    h->a.f = h->state;
+}
+
+// Two fused steps t, t + 1 (t even) outside a graph.
+cudaError_t launch_pair_at(lbm_s* h, long t) {
+    lbm::Args a = h->a;
+    if (a.rseed) {
+        a.rbase = lbm::round_hash(a.rseed, static_cast<unsigned long long>(t));
+        a.rbase1 = lbm::round_hash(a.rseed, static_cast<unsigned long long>(t + 1));
+        a.rtable = nullptr;
+        a.tstep = 0;
+    }
+    cudaError_t e = launch_fused(h, a, h->state_alt, h->stream);
+    if (e == cudaSuccess) swap_arrays(h);
+    return e;
+}
+
+// Error word of the fused kernel (a tile load that timed out), read after a
+// synchronisation; cleared once reported.
+int fused_error(lbm_s* h) {
+    if (!h->d_err) return LBM_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
+    if (v == 0) return LBM_OK;
+    cudaMemset(h->d_err, 0, sizeof(int));
+    return lbm::set_error(LBM_ECUDA, "a fused two-step launch timed out waiting for its tile load; the state is invalid");
+}
+
+// Steps per graph replay: a multiple of 4 with fused steps (an even number of
+// fused launches ends on the array the graph started from).
+int graph_len(const lbm_s* h) { return fused_active(h) ? (h->graph_steps / 4) * 4 : h->graph_steps; }
 
 // rtable[k] = the hash of (seed, t0 + k) for the k-th launch of a graph replay.
 __global__ void fill_round_table(unsigned* rtable, unsigned long long seed, unsigned long long t0, int n) {
@@ -149,7 +286,7 @@ cudaError_t capture_graph(lbm_s* h, int fm) {
     if (e == cudaSuccess && !h->ev_in) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess && !h->ev_out) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
-    if (h->a.rseed && h->rtable_cap < h->graph_steps) {  // one hash per launch of a replay
+    if (h->a.rseed && h->rtable_cap < h->graph_steps) {  // one hash per step of a replay
         if (h->d_rtable) cudaFree(h->d_rtable);             // (synchronous: no replay still reads it)
         h->d_rtable = nullptr;
         h->rtable_cap = 0;
@@ -158,10 +295,26 @@ cudaError_t capture_graph(lbm_s* h, int fm) {
         h->rtable_cap = h->graph_steps;
     }
     cudaGraph_t g = nullptr;
+    const bool fused = fused_active(h);
+    if (fused) e = ensure_fused(h);
+    if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k) {
+    const int len = graph_len(h);
+    if (fused) {  // len / 2 fused launches, alternating between the two arrays
+        for (int k = 0; k < len / 2 && e == cudaSuccess; ++k) {
+            lbm::Args ak = h->a;
+            ak.f = (k & 1) ? h->state_alt : h->state;
+            if (ak.rseed) {
+                ak.rtable = h->d_rtable;
+                ak.tstep = 2 * k;
+            }
+            e = launch_fused(h, ak, (k & 1) ? h->state : h->state_alt, h->gstream);
+        }
+    }
+    for (int k = 0; !fused && k < len && e == cudaSuccess; ++k) {
         lbm::Args ak = h->a;
+        ak.variant = single_variant(h);
         if (ak.rseed) {
             ak.rtable = h->d_rtable;
             ak.tstep = k;
@@ -188,8 +341,8 @@ cudaError_t replay_graph(lbm_s* h) {
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_in, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gstream, h->ev_in, 0);
     if (e == cudaSuccess && h->a.rseed) {
-        fill_round_table<<<(h->graph_steps + 255) / 256, 256, 0, h->gstream>>>(
-            h->d_rtable, h->a.rseed, static_cast<unsigned long long>(h->t), h->graph_steps);
+        fill_round_table<<<(graph_len(h) + 255) / 256, 256, 0, h->gstream>>>(
+            h->d_rtable, h->a.rseed, static_cast<unsigned long long>(h->t), graph_len(h));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(h->graph, h->gstream);
@@ -203,7 +356,7 @@ int stats_into(lbm_s* h, double out[3]) {
              "stats kernel");
     LBM_CUDA(cudaMemcpyAsync(out, h->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "stats copy");
     LBM_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
-    return LBM_OK;
+    return fused_error(h);
 }
 
 int after_reset(lbm_s* h) {
@@ -331,6 +484,8 @@ int lbm_destroy(lbm_t h) {
         if (h->ffield) cudaFree(h->ffield);
         if (h->partials) cudaFree(h->partials);
         if (h->d_rtable) cudaFree(h->d_rtable);
+        if (h->state_alt) cudaFree(h->state_alt);
+        if (h->d_err) cudaFree(h->d_err);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "lbm_destroy");
     }
@@ -388,25 +543,43 @@ int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed) {
     return LBM_OK;
 }
 
-// Variants the storage kind admits: 0 for FP64, 0-1 for FP32, 0-2 for 16-bit.
-static int variant_count(int store) {
-    return store == LBM_F64 ? 1 : (store == LBM_F32 ? 2 : 3);
+// Variants the storage kind admits: 0 for FP64; 0, 1 and 3 for FP32; 0-3 for 16-bit.
+static bool variant_allowed(int store, int v) {
+    if (store == LBM_F64) return v == 0;
+    if (store == LBM_F32) return v == 0 || v == 1 || v == 3;
+    return v >= 0 && v <= 3;
 }
 
 int lbm_set_variant(lbm_t h, int variant) {
     CHECK_HANDLE(h);
-    if (variant < 0 || variant > 2) return fail(LBM_EINVAL, "variant must be 0, 1 or 2");
-    h->a.variant = variant < variant_count(h->store) ? variant : 0;
+    if (variant < 0 || variant > 3) return fail(LBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    const int v = variant_allowed(h->store, variant) ? variant : 0;
+    if (v == 3) LBM_CUDA(ensure_fused(h), "second population array for fused steps");
+    h->a.variant = v;
     return LBM_OK;
 }
 
-int lbm_tune(lbm_t h, int trial_steps, float ms[3]) {
+int lbm_tune(lbm_t h, int trial_steps, float ms[4]) {
     CHECK_HANDLE(h);
     if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1");
     const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
-    if (ms) ms[0] = ms[1] = ms[2] = 0.f;
-    const int nvar = variant_count(h->store);
+    if (ms) ms[0] = ms[1] = ms[2] = ms[3] = 0.f;
     static const int widths[4] = {128, 256, 64, 32};  // CTA shapes 128x2, 256x1, 64x4, 32x8
+    const int v_prev = h->a.variant;
+    // `steps` steps from step h->t as lbm_step takes them without graphs
+    auto run = [&](int k0, int count) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (long t = h->t + k0, end = h->t + k0 + count; t < end && e == cudaSuccess;) {
+            if (fused_active(h) && (t & 1) == 0 && end - t >= 2) {
+                e = launch_pair_at(h, t);
+                t += 2;
+            } else {
+                e = launch_step_at(h, (t & 1) != 0, t);
+                t += 1;
+            }
+        }
+        return e;
+    };
     void* backup = nullptr;
     LBM_CUDA(cudaMallocAsync(&backup, h->state_bytes, h->stream), "tune snapshot allocation");
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -415,14 +588,19 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[3]) {
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = 0, best_w = 128;
-    for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+        if (!variant_allowed(h->store, v)) continue;
+        if (v == 3 && (ensure_fused(h) != cudaSuccess || h->check_every != 0)) {
+            cudaGetLastError();  // no room for the second array: variant 3 is not a candidate
+            continue;
+        }
         float best_of_v = 1e30f;
-        for (int wi = 0; wi < 4 && e == cudaSuccess; ++wi) {
+        for (int wi = 0; wi < (v == 3 ? 1 : 4) && e == cudaSuccess; ++wi) {  // variant 3 has a fixed tile
             h->a.variant = v;
             h->a.block_x = widths[wi];
-            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+            e = run(0, 2);
             if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
-            for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_step(h, ((h->t + k) & 1) != 0);
+            if (e == cudaSuccess) e = run(2, steps);
             if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(t1);
             float t = 0.f;
@@ -435,7 +613,7 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[3]) {
         }
         if (ms && e == cudaSuccess) ms[v] = best_of_v;
     }
-    h->a.variant = best_v;
+    h->a.variant = e == cudaSuccess ? best_v : v_prev;
     h->a.block_x = best_w;
     cudaFreeAsync(backup, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -530,11 +708,20 @@ int lbm_init(lbm_t h, const double* rho, const double* u) {
 int lbm_step(lbm_t h, long n) {
     CHECK_HANDLE(h);
     if (n < 0) return fail(LBM_EINVAL, "step count must be >= 0");
+    const bool fused = fused_active(h);
+    if (fused) LBM_CUDA(ensure_fused(h), "second population array for fused steps");
     for (long s = 0; s < n;) {
-        if (h->graph_steps > 0 && h->check_every == 0 && (h->t & 1) == 0 && n - s >= h->graph_steps) {
+        const int len = graph_len(h);
+        if (len > 0 && h->check_every == 0 && (h->t & 1) == 0 && n - s >= len) {
             LBM_CUDA(replay_graph(h), "step graph");
-            h->t += h->graph_steps;
-            s += h->graph_steps;
+            h->t += len;
+            s += len;
+            continue;
+        }
+        if (fused && (h->t & 1) == 0 && n - s >= 2) {
+            LBM_CUDA(launch_pair_at(h, h->t), "fused step launch");
+            h->t += 2;
+            s += 2;
             continue;
         }
         LBM_CUDA(launch_step(h, (h->t & 1) != 0), "step kernel launch");
@@ -570,7 +757,7 @@ int lbm_macros(lbm_t h, double* rho, double* u) {
         LBM_CUDA(lbm::launch_macros(h->a, h->store, h->t & 1, h->walls, force_mode(h), mrho, mu, h->stream),
                  "macros kernel");
         LBM_CUDA(cudaStreamSynchronize(h->stream), "macros sync");
-        return LBM_OK;
+        return fused_error(h);
     }
     DevBuf buf(h->stream);
     LBM_CUDA(buf.alloc(3 * n * sizeof(double)), "macros staging");
@@ -582,7 +769,7 @@ int lbm_macros(lbm_t h, double* rho, double* u) {
     if (rho) LBM_CUDA(cudaMemcpyAsync(rho, drho, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "rho copy");
     if (u) LBM_CUDA(cudaMemcpyAsync(u, du, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "u copy");
     LBM_CUDA(cudaStreamSynchronize(h->stream), "macros sync");
-    return LBM_OK;
+    return fused_error(h);
 }
 
 // Eq. (28)-(30) divide by the rates at which the second-order moments relax:
@@ -632,7 +819,7 @@ int lbm_get_f(lbm_t h, double* f) {
              "get_f kernel");
     LBM_CUDA(cudaMemcpyAsync(f, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "f copy");
     LBM_CUDA(cudaStreamSynchronize(h->stream), "get_f sync");
-    return LBM_OK;
+    return fused_error(h);
 }
 
 int lbm_set_f_device(lbm_t h, const double* f) {

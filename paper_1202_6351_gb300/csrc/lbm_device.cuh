@@ -151,10 +151,11 @@ enum : int { kCorner = 4 };
 
 struct Args {
     void* f;                  // populations [9][ny][pitch] of the stored type
-    void* fo;                 // where the one-node kernels store the step's result; null: f (in place).
+    void* fo;                 // where an out-of-place step stores its result (null: f, in place).
                               // Every slot is read and written by one thread, so a step from f into a
                               // second array of the same layout needs no other change (the adjoint
-                              // recomputes its checkpoint segments this way instead of copying)
+                              // recomputes its checkpoint segments this way instead of copying); only
+                              // the kernels instantiated with OOP read it
     long long plane;          // pitch * ny
     int nx, ny, pitch;
     int wall[4];              // 1 if the edge (W, E, S, N) is a wall
@@ -180,6 +181,7 @@ struct Args {
     const unsigned* rtable;
     unsigned rbase;
     int tstep;
+    unsigned rbase1;          // C0 of the second step of a two-step launch (rtable[tstep + 1] in a replay)
 };
 
 // Fill Args::kf, kd, wallxf, wallyf from om, rho0, F, wallx, wally (and zero
@@ -315,14 +317,14 @@ __device__ __forceinline__ unsigned round_node(const Args& a, unsigned base, int
 // rb: the hash C0 of this launch's (seed, step) when SR (stochastic rounding).
 // For FP32 storage with SR, err[q] is the exact remainder of d[q] (the
 // collision's two_sum), which round_sr32 rounds in.
-template <int STORE, bool ODD, bool WALLS, bool SR = false>
+template <int STORE, bool ODD, bool WALLS, bool SR = false, bool OOP = false>
 __device__ __forceinline__ void store_node(const Args& a, int x, int y, const typename Store<STORE>::R d[9],
                                            unsigned rb, const typename Store<STORE>::R* err = nullptr) {
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     constexpr bool SR32 = SR && STORE == LBM_F32;
-    T* __restrict__ f = static_cast<T*>(a.fo ? a.fo : a.f);
+    T* __restrict__ f = static_cast<T*>(OOP ? a.fo : a.f);
     const int n = y * a.pitch + x;
     const unsigned rn = SR ? round_node(a, rb, x, y) : 0u;
     auto put = [&](R v, R e, int q) -> T {
@@ -640,7 +642,8 @@ LBM_HD void collide(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) {
 // a1-a9: AA-pattern load, decode, force, collision, encode, AA-pattern store.
 // With SR on FP32 storage the collision keeps the exact remainder of each
 // post-collision value for the stochastic rounding of the store.
-template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false>
+// OOP: store into a.fo instead of a.f (an out-of-place step).
+template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS, bool SR = false, bool OOP = false>
 __device__ __forceinline__ void step_node(const Args& a, int x, int y, unsigned rb) {
     using R = typename Store<STORE>::R;
     constexpr bool TS = SR && STORE == LBM_F32;
@@ -650,7 +653,7 @@ __device__ __forceinline__ void step_node(const Args& a, int x, int y, unsigned 
     R Fx, Fy;
     node_force<R, FORCE>(a, x, y, Fx, Fy);
     collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, err);
-    store_node<STORE, ODD, WALLS, SR>(a, x, y, d, rb, err);
+    store_node<STORE, ODD, WALLS, SR, OOP>(a, x, y, d, rb, err);
 }
 
 // As step_node; with walls, only nodes on the lattice edge take the wall-aware

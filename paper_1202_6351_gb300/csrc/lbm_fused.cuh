@@ -1,0 +1,310 @@
+// lbm_fused.cuh -- two time steps per launch (temporal blocking) for FP32 and
+// 16-bit storage: one HBM read and one HBM write of the populations per two
+// collide-and-stream steps (Eq. 23-24) instead of one of each per step.
+//
+// A CTA owns a TX x TY tile of nodes.  Two steps need the tile's state at time
+// t on the tile grown by two nodes on every side, so:
+//   1. one TMA load (cp.async.bulk.tensor.3d) brings all nine population
+//      planes of that region, f(t), into shared memory (the box starts at a
+//      16-byte aligned column left of the region; periodic wrap-around, which
+//      a tensor copy does not do, is patched with plain loads on edge tiles);
+//   2. every node of the grown region collides in place (step t: collision of
+//      Sec. II, rounded to the storage format exactly as the one-step kernel
+//      stores it);
+//   3. every node of the tile grown by one node pulls its populations from its
+//      neighbours in shared memory, with the wall links of Sec. III-A/C, and
+//      collides (step t + 1) into a second shared buffer;
+//   4. every node of the tile pulls f(t + 2) from that buffer and writes it to
+//      the output array in the natural layout.
+// The per-node arithmetic and every rounding of the stored values are those of
+// two single steps (AA even step then odd step), so the result is bit for bit
+// that of lbm_step without fusion; nodes of the grown regions are computed by
+// more than one CTA (about 1.24x the collisions of two single steps for a
+// 64 x 16 tile).  The input and output arrays differ (ping-pong): neighbouring
+// CTAs read the halo of this CTA's tile while it writes.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <int STORE> struct FusedTile;
+template <> struct FusedTile<LBM_F32> {
+    static constexpr int TX = 64, TY = 16, ALIGN = 4, THREADS = 512, MIN_BLOCKS = 2;
+};
+template <> struct FusedTile<LBM_F16DEV> {
+    static constexpr int TX = 64, TY = 16, ALIGN = 8, THREADS = 256, MIN_BLOCKS = 4;
+};
+template <> struct FusedTile<LBM_BF16DEV> : FusedTile<LBM_F16DEV> {};
+
+// Shared-memory geometry of the fused kernel for one storage kind.
+template <int STORE>
+struct FusedGeom {
+    using FT = FusedTile<STORE>;
+    using T = typename Store<STORE>::T;
+    static constexpr int TX = FT::TX, TY = FT::TY;
+    static constexpr int BW = TX + 2 * FT::ALIGN;   // box width (elements): 16-byte aligned on both sides
+    static constexpr int BH = TY + 4;               // box height: two halo rows above and below
+    static constexpr int OFF = FT::ALIGN - 2;       // column of region x = x0 - 2 inside the box
+    static constexpr int RW = TX + 4, RH = TY + 4;  // region collided at step t
+    static constexpr int SW = TX + 2, SH = TY + 2;  // region collided at step t + 1
+    static constexpr size_t A_BYTES = size_t(9) * BH * BW * sizeof(T);
+    static constexpr size_t B_BYTES = size_t(9) * SH * SW * sizeof(T);
+    static constexpr size_t SMEM = A_BYTES + B_BYTES;
+    static_assert((BW * sizeof(T)) % 16 == 0 && (FT::ALIGN * sizeof(T)) == 16, "TMA box alignment");
+    static_assert(A_BYTES % 128 == 0, "second buffer alignment");
+};
+
+// ---------------------------------------------------------------- TMA and mbarrier (inline PTX)
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit_ns` nanoseconds
+// (globaltimer); returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+          "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Error codes the fused kernel leaves in its error word.
+enum : int { kFusedErrTimeout = 1 };
+
+// ---------------------------------------------------------------- the kernel
+// a.f is the input array (natural layout at the even step t), `out` the output
+// array (f(t + 2), natural layout); `map` describes a.f as a 3-D tensor
+// [9][ny][nx] with row pitch a.pitch.  With stochastic rounding the hashes of
+// steps t and t + 1 are a.rbase and a.rbase1, or a.rtable[a.tstep] and
+// a.rtable[a.tstep + 1] in a graph replay.
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+__global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::MIN_BLOCKS)
+    fused2_kernel(const __grid_constant__ CUtensorMap map, const Args a, void* __restrict__ out,
+                  int* __restrict__ err) {
+    using G = FusedGeom<STORE>;
+    using S = Store<STORE>;
+    using T = typename S::T;
+    using R = typename S::R;
+    constexpr bool TS = SR && STORE == LBM_F32;
+    constexpr int NT = FusedTile<STORE>::THREADS;
+    extern __shared__ __align__(1024) unsigned char fused_smem[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int ok;
+    T* A = reinterpret_cast<T*>(fused_smem);
+    T* B = reinterpret_cast<T*>(fused_smem + G::A_BYTES);
+    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    const int tid = threadIdx.x;
+    const bool perx = !a.wall[LBM_WEST], pery = !a.wall[LBM_SOUTH];
+
+    // ---- 1. the region's state at time t
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, static_cast<unsigned>(G::A_BYTES));
+        tma_load_3d(A, &map, x0 - FusedTile<STORE>::ALIGN, y0 - 2, 0, &bar);
+        bool done = mbar_wait_bounded(&bar, 0, 1000000000ull);  // 1 s
+        if (!done) {
+            atomicOr(err, kFusedErrTimeout);
+            mbar_wait_bounded(&bar, 0, 4000000000ull);  // let the copy land before the CTA exits
+        }
+        ok = done ? 1 : 0;
+    }
+    __syncthreads();
+    if (!ok) return;
+    auto Aat = [&](int q, int ry, int rxb) -> T& { return A[(q * G::BH + ry) * G::BW + rxb]; };
+    auto Bat = [&](int q, int sy, int sx) -> T& { return B[(q * G::SH + sy) * G::SW + sx]; };
+    // Region coordinates lie in [-2, n + TX + 1]: one addition or subtraction of
+    // n wraps them when n > TX + 2 (TY + 2 along y); smaller lattices take the modulo.
+    const bool small = a.nx <= G::TX + 2 || a.ny <= G::TY + 2;
+    auto wrap = [small](int v, int n) {
+        if (small) return ((v % n) + n) % n;
+        return v < 0 ? v + n : (v >= n ? v - n : v);
+    };
+
+    // periodic wrap-around of the region's halo (edge tiles only)
+    if ((perx && (x0 - 2 < 0 || x0 + G::TX + 2 > a.nx)) || (pery && (y0 - 2 < 0 || y0 + G::TY + 2 > a.ny))) {
+        const T* __restrict__ f = static_cast<const T*>(a.f);
+        for (int k = tid; k < 9 * G::RW * G::RH; k += NT) {
+            const int q = k / (G::RW * G::RH), r = k % (G::RW * G::RH);
+            const int ry = r / G::RW, rx = r % G::RW;
+            int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+            const bool outx = gx < 0 || gx >= a.nx, outy = gy < 0 || gy >= a.ny;
+            if (!((outx && perx) || (outy && pery))) continue;
+            if ((outx && !perx) || (outy && !pery)) continue;  // beyond a wall: never used
+            gx = ((gx % a.nx) + a.nx) % a.nx;
+            gy = ((gy % a.ny) + a.ny) % a.ny;
+            Aat(q, ry, rx + G::OFF) = f[q * a.plane + (long long)gy * a.pitch + gx];
+        }
+        __syncthreads();
+    }
+
+    const Coef<R> c(a);
+    const unsigned rb0 = SR ? (a.rtable ? a.rtable[a.tstep] : a.rbase) : 0u;
+    const unsigned rb1 = SR ? (a.rtable ? a.rtable[a.tstep + 1] : a.rbase1) : 0u;
+    // ---- 2. step t: collide the grown region in place (AA even step: plain stores)
+    for (int k = tid; k < G::RW * G::RH; k += NT) {
+        const int ry = k / G::RW, rx = k % G::RW;
+        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
+        gx = wrap(gx, a.nx);
+        gy = wrap(gy, a.ny);
+        R d[9], e[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] = S::dec(Aat(q, ry, rx + G::OFF));
+        R Fx, Fy;
+        node_force<R, FORCE>(a, gx, gy, Fx, Fy);
+        collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
+        const unsigned rn = SR ? round_node(a, rb0, gx, gy) : 0u;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+            T v;
+            if constexpr (TS) v = round_sr32(d[q], e[q], r);
+            else if constexpr (SR) v = enc_sr<STORE>(d[q], r);
+            else v = S::enc(d[q]);
+            Aat(q, ry, rx + G::OFF) = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. step t + 1 on the tile grown by one node (AA odd step: pull with
+    // the wall links, wall terms added before the rounding of the store)
+    for (int k = tid; k < G::SW * G::SH; k += NT) {
+        const int sy = k / G::SW, sx = k % G::SW;
+        int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
+        if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
+        gx = wrap(gx, a.nx);
+        gy = wrap(gy, a.ny);
+        const int ry = sy + 1, rxb = sx + 1 + G::OFF;
+        R d[9], e[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
+            if (w >= 0) d[q] = S::dec(Aat(opp(q), ry, rxb)) + wall_term<R>(a, q, w);
+            else d[q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
+        }
+        R Fx, Fy;
+        node_force<R, FORCE>(a, gx, gy, Fx, Fy);
+        collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
+        const unsigned rn = SR ? round_node(a, rb1, gx, gy) : 0u;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+            const int w = WALLS ? incoming_wall(a, opp(q), gx, gy) : -1;
+            R v = d[q], ev = TS ? e[q] : R(0);
+            if (w >= 0) {
+                if constexpr (TS) {
+                    float e2;
+                    v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
+                    ev = e[q] + e2;
+                } else {
+                    v = d[q] + wall_term<R>(a, opp(q), w);
+                }
+            }
+            T o;
+            if constexpr (TS) o = round_sr32(v, ev, r);
+            else if constexpr (SR) o = enc_sr<STORE>(v, r);
+            else o = S::enc(v);
+            Bat(q, sy, sx) = o;
+        }
+    }
+    __syncthreads();
+
+    // ---- 4. f(t + 2) of the tile: pull from the second buffer, natural layout
+    T* __restrict__ fo = static_cast<T*>(out);
+    for (int k = tid; k < G::TX * G::TY; k += NT) {
+        const int ty = k / G::TX, tx = k % G::TX;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= a.nx || gy >= a.ny) continue;
+        const long long n = (long long)gy * a.pitch + gx;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
+            fo[q * a.plane + n] = w >= 0 ? Bat(opp(q), ty + 1, tx + 1) : Bat(q, ty + 1 - cy(q), tx + 1 - cx(q));
+        }
+    }
+}
+
+}  // namespace lbm
+
+namespace lbm {
+
+// Launch of the fused kernel for one storage kind (dynamic shared memory set
+// up on first use of each instantiation).
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+static cudaError_t launch_fused_one(const CUtensorMap& map, const Args& a, void* out, int* err, cudaStream_t s) {
+    using G = FusedGeom<STORE>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<MODEL, STORE, FORCE, WALLS, SR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid((a.nx + G::TX - 1) / G::TX, (a.ny + G::TY - 1) / G::TY);
+    fused2_kernel<MODEL, STORE, FORCE, WALLS, SR><<<grid, FusedTile<STORE>::THREADS, G::SMEM, s>>>(map, a, out, err);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int STORE, int FORCE, bool WALLS>
+static cudaError_t launch_fused_sr(const CUtensorMap& map, const Args& a, void* out, int* err, cudaStream_t s) {
+    return a.rseed ? launch_fused_one<MODEL, STORE, FORCE, WALLS, true>(map, a, out, err, s)
+                   : launch_fused_one<MODEL, STORE, FORCE, WALLS, false>(map, a, out, err, s);
+}
+
+template <int MODEL, int STORE, int FORCE>
+static cudaError_t launch_fused_walls(const CUtensorMap& map, const Args& a, void* out, int* err, bool walls,
+                                      cudaStream_t s) {
+    return walls ? launch_fused_sr<MODEL, STORE, FORCE, true>(map, a, out, err, s)
+                 : launch_fused_sr<MODEL, STORE, FORCE, false>(map, a, out, err, s);
+}
+
+template <int MODEL, int STORE>
+static cudaError_t launch_fused_force(const CUtensorMap& map, const Args& a, void* out, int* err, int force,
+                                      bool walls, cudaStream_t s) {
+    switch (force) {
+        case 0: return launch_fused_walls<MODEL, STORE, 0>(map, a, out, err, walls, s);
+        case 1: return launch_fused_walls<MODEL, STORE, 1>(map, a, out, err, walls, s);
+        default: return launch_fused_walls<MODEL, STORE, 2>(map, a, out, err, walls, s);
+    }
+}
+
+template <int STORE>
+static cudaError_t launch_fused_store(const CUtensorMap& map, const Args& a, void* out, int* err, int model,
+                                      int force, bool walls, cudaStream_t s) {
+    switch (model) {
+        case LBM_CASCADED: return launch_fused_force<LBM_CASCADED, STORE>(map, a, out, err, force, walls, s);
+        case LBM_BGK: return launch_fused_force<LBM_BGK, STORE>(map, a, out, err, force, walls, s);
+        default: return launch_fused_force<LBM_RAWMRT, STORE>(map, a, out, err, force, walls, s);
+    }
+}
+
+}  // namespace lbm

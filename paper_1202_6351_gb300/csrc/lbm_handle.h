@@ -35,4 +35,11 @@ struct lbm_s {
     // C0 of a graph replay, filled on the graph stream before each replay.
     unsigned* d_rtable = nullptr;
     int rtable_cap = 0;
+    // Two fused steps per launch (variant 3): the second population array of
+    // the ping-pong, a TMA descriptor of each array (tmap[k] describes
+    // tmap_ptr[k]) and the kernels' error word.  Allocated on first use.
+    void* state_alt = nullptr;
+    CUtensorMap tmap[2];
+    void* tmap_ptr[2] = {nullptr, nullptr};
+    int* d_err = nullptr;
 };

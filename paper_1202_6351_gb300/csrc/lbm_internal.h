@@ -1,6 +1,7 @@
 // lbm_internal.h -- host-side declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -24,6 +25,15 @@ cudaError_t launch_step_f64(const Args& a, int model, bool odd, int force, bool 
 cudaError_t launch_step_f32(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
 cudaError_t launch_step_bf16(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
 cudaError_t launch_step_f16(const Args& a, int model, bool odd, int force, bool walls, cudaStream_t s);
+
+// Two fused steps (variant 3, lbm_fused.cuh) from a.f (natural layout, even
+// step) into `out`; `map` describes a.f.  FP32, BF16 and FP16 storage.
+cudaError_t launch_fused_f32(const CUtensorMap& map, const Args& a, void* out, int* err, int model, int force,
+                             bool walls, cudaStream_t s);
+cudaError_t launch_fused_bf16(const CUtensorMap& map, const Args& a, void* out, int* err, int model, int force,
+                              bool walls, cudaStream_t s);
+cudaError_t launch_fused_f16(const CUtensorMap& map, const Args& a, void* out, int* err, int model, int force,
+                             bool walls, cudaStream_t s);
 
 // Auxiliary kernels (lbm_aux.cu); every field argument is dense [..][ny][nx] FP64 device memory.
 cudaError_t launch_init(const Args& a, int store, int model, int force, const double* rho, const double* u,

@@ -25,6 +25,16 @@ __global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel(const Args a) {
     step_node_split<MODEL, STORE, ODD, FORCE, WALLS, SR>(a, x, y, SR ? round_base(a) : 0u);
 }
 
+// One node per thread from a.f into a.fo (out of place; periodic lattices,
+// FP32 and FP64 storage: the adjoint's forward and recomputed steps).
+template <int MODEL, int STORE, bool ODD, int FORCE, bool SR>
+__global__ void __launch_bounds__(kStepBX * kStepBY) step_kernel_oop(const Args a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    step_node<MODEL, STORE, ODD, FORCE, false, SR, true>(a, x, y, SR ? round_base(a) : 0u);
+}
+
 // Two rows per thread (nodes (x, y) and (x, y + 1)) with packed FP32x2
 // arithmetic; a pair that touches a wall edge takes the per-node wall path.
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
@@ -85,6 +95,16 @@ static cudaError_t launch_vec(const Args& a, cudaStream_t s) {
 
 template <int MODEL, int STORE, bool ODD, int FORCE, bool WALLS>
 static cudaError_t launch_one(const Args& a, cudaStream_t s) {
+    if (a.fo) {  // out of place: periodic FP32 / FP64 only
+        if constexpr ((STORE == LBM_F32 || STORE == LBM_F64) && !WALLS) {
+            const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
+            const dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
+            if (a.rseed) step_kernel_oop<MODEL, STORE, ODD, FORCE, true><<<grid, block, 0, s>>>(a);
+            else step_kernel_oop<MODEL, STORE, ODD, FORCE, false><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
     if constexpr (STORE == LBM_F32) {
         if (a.rseed) {  // stochastic rounding of FP32 stores: variant 0 only
             const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
@@ -96,15 +116,15 @@ static cudaError_t launch_one(const Args& a, cudaStream_t s) {
     if constexpr (STORE == LBM_F16DEV || STORE == LBM_BF16DEV) {
         if (a.rseed) {  // stochastic rounding: variants 0 and 2 (variant 1 runs variant 0)
             if constexpr (FORCE != 2) {
-                if (a.variant == 2 && !a.fo) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, true>(a, s);
+                if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, true>(a, s);
             }
             const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
             const dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
             step_kernel<MODEL, STORE, ODD, FORCE, WALLS, true><<<grid, block, 0, s>>>(a);
             return cudaGetLastError();
         }
-        if constexpr (FORCE != 2) {  // the four-node kernel steps in place only
-            if (a.variant == 2 && !a.fo) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, false>(a, s);
+        if constexpr (FORCE != 2) {
+            if (a.variant == 2) return launch_vec<4, MODEL, STORE, ODD, FORCE, WALLS, false>(a, s);
         }
     }
     const dim3 block = fit_block(a.block_x > 0 ? a.block_x : kStepBX, a.nx);
