@@ -239,10 +239,18 @@ __device__ __forceinline__ int incoming_wall(const Args& a, int q, int x, int y)
     return wy >= 0 ? (wx >= 0 ? int(kCorner) : wy) : wx;
 }
 // Moving-wall term for a population entering in direction q through wall w.
+// The product is rounded on its own (never fused into an FMA with a later
+// addition), so every kernel that adds the term rounds it alike.
 template <typename R>
 __device__ __forceinline__ R wall_term(const Args& a, int q, int w) {
-    if constexpr (sizeof(R) == 4) return wgt<R>(q) * (R(cx(q)) * a.wallxf[w] + R(cy(q)) * a.wallyf[w]);
-    else return wgt<R>(q) * (R(cx(q)) * a.wallx[w] + R(cy(q)) * a.wally[w]);  // FP64 storage: scale 1
+    if constexpr (sizeof(R) == 4) return __fmul_rn(wgt<R>(q), R(cx(q)) * a.wallxf[w] + R(cy(q)) * a.wallyf[w]);
+    else return __dmul_rn(wgt<R>(q), R(cx(q)) * a.wallx[w] + R(cy(q)) * a.wally[w]);  // FP64 storage: scale 1
+}
+// v + wall_term, one rounded addition (the moving-wall link of Sec. III-C).
+template <typename R>
+__device__ __forceinline__ R add_wall_term(const Args& a, R v, int q, int w) {
+    if constexpr (sizeof(R) == 4) return __fadd_rn(v, wall_term<R>(a, q, w));
+    else return __dadd_rn(v, wall_term<R>(a, q, w));
 }
 
 // ---------------------------------------------------------------- AA access
@@ -274,7 +282,7 @@ __device__ __forceinline__ void load_node(const Args& a, int x, int y, typename 
             int w = -1;
             if (WALLS) w = incoming_wall(a, q, x, y);
             if (w >= 0) {
-                d[q] = S::dec(plane_ptr(a, f, q)[n]) + wall_term<R>(a, q, w);
+                d[q] = add_wall_term<R>(a, S::dec(plane_ptr(a, f, q)[n]), q, w);
             } else {
                 const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
                 const int sr = cy(q) == 1 ? rm : (cy(q) == -1 ? rp : r0);
@@ -350,7 +358,7 @@ __device__ __forceinline__ void store_node(const Args& a, int x, int y, const ty
                     const float v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
                     plane_ptr(a, f, opp(q))[n] = put(v, err[q] + e2, q);
                 } else {
-                    plane_ptr(a, f, opp(q))[n] = enc(d[q] + wall_term<R>(a, opp(q), w), q);
+                    plane_ptr(a, f, opp(q))[n] = enc(add_wall_term<R>(a, d[q], opp(q), w), q);
                 }
             } else {
                 const int tx = cx(q) == 1 ? xp : (cx(q) == -1 ? xm : x);

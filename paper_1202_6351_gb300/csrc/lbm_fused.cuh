@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
-            if (w >= 0) d[q] = S::dec(Aat(opp(q), ry, rxb)) + wall_term<R>(a, q, w);
+            if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(opp(q), ry, rxb)), q, w);
             else d[q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
         }
         R Fx, Fy;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
                     v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
                     ev = e[q] + e2;
                 } else {
-                    v = d[q] + wall_term<R>(a, opp(q), w);
+                    v = add_wall_term<R>(a, d[q], opp(q), w);
                 }
             }
             T o;

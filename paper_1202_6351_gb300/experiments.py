@@ -173,6 +173,44 @@ def max_stable_cell_reynolds(model, n, U=0.1, cell_res=None, convective_times=20
     return _threshold(cell_res, [ok for _, ok, _ in result]), result
 
 
+def max_stable_cell_reynolds_refined(model, n, U=0.1, lo=4.0, hi=400.0, first=16, per_round=8, rounds=3,
+                                     convective_times=20.0, store=lbm.F32):
+    """max_stable_cell_reynolds with the threshold bracketed ever more finely:
+    `first` candidates log-spaced in [lo, hi], then `rounds` times `per_round`
+    candidates log-spaced inside the bracket [last stable, first unstable] of
+    the round before (all candidates of a round run in one batch).  After the
+    default three rounds the bracket is about 1/512 of the first one in log
+    space (a few tenths of a percent).  Returns (threshold, first unstable
+    value, every (Re_c, stable, max |u|) tried)."""
+    steps = int(convective_times * n / U)
+    tried = []
+
+    def run(values):
+        res = _cavity_sweep(model, n, [(U / rc, U) for rc in values], steps, store)
+        out = [(rc, ok, umax) for rc, (ok, umax) in zip(values, res)]
+        tried.extend(out)
+        return out
+
+    values = [float(v) for v in np.exp(np.linspace(math.log(lo), math.log(hi), first))]
+    res = run(values)
+    stable, unstable = lo, None
+    for rc, ok, _ in res:
+        if not ok:
+            unstable = rc
+            break
+        stable = rc
+    if unstable is None:
+        return stable, None, tried
+    for _ in range(rounds):
+        inner = [float(v) for v in np.exp(np.linspace(math.log(stable), math.log(unstable), per_round + 2))[1:-1]]
+        for rc, ok, _ in run(inner):
+            if not ok:
+                unstable = rc
+                break
+            stable = rc
+    return stable, unstable, tried
+
+
 def max_stable_lid_velocity(model, nu, n=26, lid_u=None, steps=50_000, store=lbm.F32):
     """Sec. V's alternative test: on a fixed coarse n x n cavity (26 x 26) at a
     fixed viscosity, the largest lid speed in `lid_u` (default: 40 values

@@ -207,3 +207,38 @@ def test_cavity_grid_convergence_second_order():
         slope = -np.polyfit(x, np.log([errs[n][k] for n in ns]), 1)[0]
         print(k, " ".join(f"{errs[n][k]:.3e}" for n in ns), f"slope {slope:.3f}")
         assert 1.8 < slope < 2.7, (k, slope)
+
+
+TABLE_IV_GRIDS = (101, 201, 401)
+
+
+@pytest.fixture(scope="module")
+def stability_thresholds():
+    """Max stable cell Re on the three grids of Table IV for the three models,
+    bracketed to a few tenths of a percent (a blow-up within 20 convective
+    times counts as unstable)."""
+    out = {}
+    for n in TABLE_IV_GRIDS:
+        for model in (lbm.BGK, lbm.RAWMRT, lbm.CASCADED):
+            th, un, _ = X.max_stable_cell_reynolds_refined(model, n)
+            out[model, n] = (th, un)
+            print(f"{n}^2 {lbm.MODEL_NAMES[model]}: stable up to {th:.2f}, unstable at {un}")
+    return out
+
+
+@pytest.mark.parametrize("n", TABLE_IV_GRIDS)
+def test_stability_thresholds_of_table_IV_on_every_grid(stability_thresholds, n):
+    """Sec. V, Table IV (14.14-14.25 / 59.40-62.34 / 148.50-199.50 for SRT / raw
+    MRT / cascaded on 101^2..401^2): SRT's limit is nearly grid independent near
+    14, raw MRT reaches several times SRT and the cascaded model about 2-3 times
+    raw MRT on every grid."""
+    srt = stability_thresholds[lbm.BGK, n][0]
+    mrt = stability_thresholds[lbm.RAWMRT, n][0]
+    casc = stability_thresholds[lbm.CASCADED, n][0]
+    paper = P.PAPER["max_cell_reynolds"]
+    k = paper["grid"].index(n)
+    print(f"{n}^2: SRT {srt:.2f} ({paper['srt'][k]}), raw MRT {mrt:.2f} ({paper['raw_mrt'][k]}), "
+          f"cascaded {casc:.2f} ({paper['cascaded'][k]})")
+    assert abs(srt - paper["srt"][k]) <= 0.06 * paper["srt"][k]
+    assert mrt >= 3.0 * srt
+    assert casc >= 1.8 * mrt
