@@ -70,11 +70,11 @@ LBM_HD void collide_cascaded_vjp(const R d[9], R Fx, R Fy, const Coef<R>& c, con
     const R inv = recip(m.rho);  // as the forward kernel: IEEE in FP64, rcp.approx in FP32
     const R px = m.jx + R(0.5) * Fx, py = m.jy + R(0.5) * Fy;
     const R ux = px * inv, uy = py * inv;
-    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), uxy = rmul(ux, uy);
     const R r3 = c.rho0 * R(1.0 / 3.0);
-    const R sxx = R(2) * Fx * ux, syy = R(2) * Fy * uy, sxy = Fx * uy + Fy * ux;
+    const R P = rmul(Fx, uy) + rmul(Fy, ux);
+    const R sxx = R(2) * Fx * ux, syy = R(2) * Fy * uy, sxy = P;
     const R sxxy = Fy * uxx + R(2) * Fx * uxy, sxyy = Fx * uyy + R(2) * Fy * uxy;
-    const R P = Fx * uy + Fy * ux;
     const R sxxyy = R(2) * uxy * P;
     const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;
     const R G3 = R(2.0 / 3.0) * m.drho + m.rho * (uxx + uyy) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy);

@@ -383,6 +383,29 @@ __device__ __forceinline__ void node_force(const Args& a, int x, int y, R& Fx, R
     }
 }
 
+// ---------------------------------------------------------------- rounded products
+// A product used by more than one later operation is rounded on its own
+// (rmul): whether the compiler would fuse such a product into one of its
+// additions (an FMA) depends on the surrounding code, so without this two
+// kernels that inline the same collision could round it differently.  With
+// it, every kernel variant rounds every node alike.
+LBM_HD float rmul(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    volatile float p = a * b;
+    return p;
+#endif
+}
+LBM_HD double rmul(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    volatile double p = a * b;
+    return p;
+#endif
+}
+
 // ---------------------------------------------------------------- moments
 template <typename R>
 struct Moments {
@@ -426,12 +449,14 @@ LBM_HD Moments<R> moments(const R d[9], R rho0) {
 template <typename R>
 LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     const R m1 = Fx, m2 = Fy;
-    const R m3 = R(6) * (Fx * ux + Fy * uy);
-    const R m4 = R(2) * (Fx * ux - Fy * uy);
-    const R m5 = Fx * uy + Fy * ux;
-    const R m6 = (R(2) - R(3) * ux * ux) * Fy - R(6) * Fx * ux * uy;
-    const R m7 = (R(2) - R(3) * uy * uy) * Fx - R(6) * Fy * uy * ux;
-    const R m8 = R(6) * ((R(3) * uy * uy - R(2)) * Fx * ux + (R(3) * ux * ux - R(2)) * Fy * uy);
+    const R fxux = rmul(Fx, ux), fyuy = rmul(Fy, uy), fxuy = rmul(Fx, uy), fyux = rmul(Fy, ux);
+    const R uxx = rmul(ux, ux), uyy = rmul(uy, uy);
+    const R m3 = R(6) * (fxux + fyuy);
+    const R m4 = R(2) * (fxux - fyuy);
+    const R m5 = fxuy + fyux;
+    const R m6 = (R(2) - R(3) * uxx) * Fy - R(6) * fxux * uy;
+    const R m7 = (R(2) - R(3) * uyy) * Fx - R(6) * fyuy * ux;
+    const R m8 = R(6) * ((R(3) * uyy - R(2)) * fxux + (R(3) * uxx - R(2)) * fyuy);
     const R k = R(1.0 / 36.0);
     S[0] = k * (R(4) * (m8 - m3));
     S[1] = k * (R(6) * m1 - m3 + R(9) * m4 + R(6) * m7 - R(2) * m8);
@@ -499,14 +524,15 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = null
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (27)
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
-    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), uxy = rmul(ux, uy);
     const R r3 = c.rho0 * R(1.0 / 3.0);
     // raw source moments, Eq. (13)
     R sxx = 0, syy = 0, sxy = 0, sxxy = 0, sxyy = 0, sxxyy = 0;
     if (FORCED) {
-        sxx = R(2) * Fx * ux; syy = R(2) * Fy * uy; sxy = Fx * uy + Fy * ux;
+        const R fxuy = rmul(Fx, uy), fyux = rmul(Fy, ux);
+        sxx = R(2) * Fx * ux; syy = R(2) * Fy * uy; sxy = fxuy + fyux;
         sxxy = Fy * uxx + R(2) * Fx * uxy; sxyy = Fx * uyy + R(2) * Fy * uxy;
-        sxxyy = R(2) * uxy * (Fx * uy + Fy * ux);
+        sxxyy = R(2) * uxy * (fxuy + fyux);
     }
     const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;  // full kappa'_xx, kappa'_yy
     // Eq. (17)-(19)
@@ -553,7 +579,7 @@ LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) 
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
-    const R usq = R(1.5) * (ux * ux + uy * uy);
+    const R usq = R(1.5) * (rmul(ux, ux) + rmul(uy, uy));
     const R w = c.w4;
     R S[9];
     if (FORCED) source(ux, uy, Fx, Fy, S);
@@ -581,7 +607,7 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
     const R inv = recip(m.rho);
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
-    const R uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
+    const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), usq = uxx + uyy;
     // orthogonal moments of d (the rest-state part w rho0 is added to m_eq's side)
     const R tr = m.kxx + m.kyy;
     const R m3 = R(3) * tr - R(4) * m.drho;
@@ -591,18 +617,20 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
     const R m7 = R(2) * m.jx - R(3) * m.kxyy;
     const R m8 = R(9) * m.kxxyy - R(6) * tr + R(4) * m.drho;
     // equilibrium moments of f_eq - w rho0
-    const R e3 = R(3) * m.rho * usq - R(2) * m.drho;
+    const R p3 = rmul(R(3) * m.rho, usq);  // shared by e3 and e8
+    const R e3 = p3 - R(2) * m.drho;
     const R e4 = m.rho * (uxx - uyy);
     const R e5 = m.rho * ux * uy;
     const R e6 = m.rho * uy;
     const R e7 = m.rho * ux;
-    const R e8 = m.drho - R(3) * m.rho * usq;
+    const R e8 = m.drho - p3;
     R s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0, s8 = 0;
     if (FORCED) {  // the m^s list before Eq. (14)
-        s3 = R(6) * (Fx * ux + Fy * uy); s4 = R(2) * (Fx * ux - Fy * uy); s5 = Fx * uy + Fy * ux;
-        s6 = (R(2) - R(3) * uxx) * Fy - R(6) * Fx * ux * uy;
-        s7 = (R(2) - R(3) * uyy) * Fx - R(6) * Fy * uy * ux;
-        s8 = R(6) * ((R(3) * uyy - R(2)) * Fx * ux + (R(3) * uxx - R(2)) * Fy * uy);
+        const R fxux = rmul(Fx, ux), fyuy = rmul(Fy, uy), fxuy = rmul(Fx, uy), fyux = rmul(Fy, ux);
+        s3 = R(6) * (fxux + fyuy); s4 = R(2) * (fxux - fyuy); s5 = fxuy + fyux;
+        s6 = (R(2) - R(3) * uxx) * Fy - R(6) * fxux * uy;
+        s7 = (R(2) - R(3) * uyy) * Fx - R(6) * fyuy * ux;
+        s8 = R(6) * ((R(3) * uyy - R(2)) * fxux + (R(3) * uxx - R(2)) * fyuy);
     }
     // change of each orthogonal moment divided by its norm D_b
     const R g3 = (-c.w3 * (m3 - e3) + (R(1) - R(0.5) * c.w3) * s3) * R(1.0 / 36.0);

@@ -54,6 +54,7 @@ __device__ __forceinline__ F2& operator-=(F2& x, F2 y) { return x = x - y; }
 __device__ __forceinline__ F2& operator-=(F2& x, P2 p) { return x = x - p; }
 
 __device__ __forceinline__ F2 recip(F2 x) { return F2(make_float2(recip(x.v.x), recip(x.v.y))); }
+__device__ __forceinline__ F2 rmul(F2 a, F2 b) { return F2(a * b); }  // rounded product (P2 -> F2)
 
 template <>
 __host__ __device__ inline F2 wgt<F2>(int q) { return F2(wgt<float>(q)); }

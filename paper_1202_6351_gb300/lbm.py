@@ -83,6 +83,18 @@ SIGNATURES = {
     "lbm_batch_info": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "lbm_stats_noalloc": (_i, [_vp, C.POINTER(lbm_layout_t), _vp, _vp]),
     "lbm_last_error": (C.c_char_p, []),
+    # D3Q27 lattices (include/lbm3d.h)
+    "lbm3_create": (_i, [_i, _i, _i, _dp, _dp, _i, _d, C.POINTER(_vp)]),
+    "lbm3_destroy": (_i, [_vp]),
+    "lbm3_set_stream": (_i, [_vp, _vp]),
+    "lbm3_init": (_i, [_vp, _vp, _vp]),
+    "lbm3_step": (_i, [_vp, _l]),
+    "lbm3_macros": (_i, [_vp, _vp, _vp]),
+    "lbm3_get_f": (_i, [_vp, _vp]),
+    "lbm3_set_f": (_i, [_vp, _vp]),
+    "lbm3_time": (_l, [_vp]),
+    "lbm3_info": (_i, [_vp, C.POINTER(C.c_long), C.POINTER(C.c_size_t), C.POINTER(_vp)]),
+    "lbm3_bytes_per_update": (C.c_size_t, [_i]),
 }
 
 
@@ -414,3 +426,80 @@ class Batch:
         _check(self.lib.lbm_batch_info(self.b, cfg, C.byref(st)))
         return {"tile": (cfg[0], cfg[1]), "policy": self.POLICIES[cfg[2]], "order": self.ORDERS[cfg[3]],
                 "grid": cfg[4], "tiles": cfg[5], "stream": st.value or 0}
+
+
+class Lattice3:
+    """A periodic D3Q27 central-moment lattice (lbm3_* of include/lbm3d.h).
+    omegas = (omega_bulk, omega_shear, omega_3, omega_4, omega_5, omega_6);
+    host arrays are numpy float64: rho [nz, ny, nx], u [3, nz, ny, nx],
+    f [27, nz, ny, nx]."""
+
+    def __init__(self, nx, ny, nz, omegas, force=(0.0, 0.0, 0.0), store=F32, rho0=1.0, stream=None):
+        self.lib = load_library()
+        self.shape = (int(nz), int(ny), int(nx))
+        self.store = int(store)
+        h = C.c_void_p()
+        _check(self.lib.lbm3_create(int(nx), int(ny), int(nz), _darr(omegas, 6), _darr(force, 3), int(store),
+                                    float(rho0), C.byref(h)))
+        self.h = h
+        if stream is not None:
+            _check(self.lib.lbm3_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if self.h is not None:
+            _check(self.lib.lbm3_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    @property
+    def time(self):
+        return int(self.lib.lbm3_time(self.h))
+
+    def init(self, rho=None, u=None):
+        rp = up = None
+        if rho is not None:
+            ra, rp = _host(rho, self.shape)
+        if u is not None:
+            ua, up = _host(u, (3,) + self.shape)
+        _check(self.lib.lbm3_init(self.h, rp, up))
+        return self
+
+    def step(self, n=1):
+        _check(self.lib.lbm3_step(self.h, int(n)))
+        return self
+
+    def macros(self):
+        rho = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        _check(self.lib.lbm3_macros(self.h, rho.ctypes.data, u.ctypes.data))
+        return rho, u
+
+    def get_f(self):
+        f = np.empty((27,) + self.shape)
+        _check(self.lib.lbm3_get_f(self.h, f.ctypes.data))
+        return f
+
+    def set_f(self, f):
+        a, p = _host(f, (27,) + self.shape)
+        _check(self.lib.lbm3_set_f(self.h, p))
+        return self
+
+    def info(self):
+        dims = (C.c_long * 5)()
+        nbytes = C.c_size_t()
+        state = C.c_void_p()
+        _check(self.lib.lbm3_info(self.h, dims, C.byref(nbytes), C.byref(state)))
+        return {"nx": dims[0], "ny": dims[1], "nz": dims[2], "pitch": dims[3], "store": dims[4],
+                "bytes": nbytes.value, "state": state.value}

@@ -112,3 +112,27 @@ def batch_domains(seed: int = 20261202, count: int = 96, side_min: int = 64, sid
             "store": "f32" if (i // 2) % 2 == 0 else "f16",
         })
     return out
+
+
+def taylor_green_3d_init(n: int, u0: float, rho0: float = 1.0):
+    """The three-dimensional Taylor-Green vortex on an n^3 periodic lattice:
+    u = u0 sin(kx) cos(ky) cos(kz), v = -u0 cos(kx) sin(ky) cos(kz), w = 0,
+    k = 2 pi / n, with the pressure of the incompressible solution,
+    p = p0 + rho0 u0^2 / 16 (cos 2kx + cos 2ky)(cos 2kz + 2), and p = rho / 3.
+    Returns rho[n, n, n] and u[3, n, n, n] (float64, axes z, y, x)."""
+    k = 2.0 * math.pi / n
+    c = np.arange(n, dtype=np.float64)
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = u0 * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z)
+    u[1] = -u0 * np.cos(k * X) * np.sin(k * Y) * np.cos(k * Z)
+    rho = rho0 + 3.0 * rho0 * u0 * u0 / 16.0 * (np.cos(2 * k * X) + np.cos(2 * k * Y)) * (np.cos(2 * k * Z) + 2.0)
+    return rho, u
+
+
+def random_fields_3d(seed: int, nx: int, ny: int, nz: int, u_amp: float = 0.05, rho_amp: float = 0.02):
+    """Uncorrelated random (rho, u) fields on an nx x ny x nz lattice (axes z, y, x)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + rho_amp * rng.standard_normal((nz, ny, nx))
+    u = u_amp * rng.standard_normal((3, nz, ny, nx))
+    return rho, u

@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library builds, loads, exports every symbol that
-include/lbm.h declares, and its host-side argument checks answer correctly.
+include/lbm.h and include/lbm3d.h declare, and its host-side argument checks
+answer correctly.
 No kernel is launched here."""
 import ctypes as C
 import os
@@ -19,7 +20,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lbm3?_\w+)\s*\(", text, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -153,3 +154,32 @@ def test_null_handles_of_the_tuning_rounding_batch_and_adjoint_calls():
     assert lib.lbm_batch_create(None, 0, C.byref(out)) == lbm.LBM_EINVAL
     assert lbm.lbm_last_error()
 
+
+
+BAD_CREATE3 = [
+    dict(nx=0), dict(nz=0), dict(nz=70000), dict(nx=2048, ny=2048, nz=1024),
+    dict(omegas=(1.0, 2.0, 1.0, 1.0, 1.0, 1.0)), dict(store=lbm.F16DEV), dict(rho0=-1.0),
+    dict(force=(float("nan"), 0.0, 0.0)),
+]
+
+
+@pytest.mark.parametrize("kw", BAD_CREATE3)
+def test_d3q27_create_rejects_bad_arguments_before_touching_the_device(kw):
+    lib = lbm.load_library()
+    args = dict(nx=4, ny=4, nz=4, omegas=(1.0,) * 6, force=(0.0, 0.0, 0.0), store=lbm.F32, rho0=1.0)
+    args.update(kw)
+    h = C.c_void_p()
+    rc = lib.lbm3_create(args["nx"], args["ny"], args["nz"], (C.c_double * 6)(*args["omegas"]),
+                         (C.c_double * 3)(*args["force"]), args["store"], args["rho0"], C.byref(h))
+    assert rc == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error().startswith("lbm3_create")
+
+
+def test_d3q27_null_handles():
+    lib = lbm.load_library()
+    assert lib.lbm3_destroy(None) == lbm.LBM_OK
+    assert lib.lbm3_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm3_macros(None, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm3_time(None) == -1
+    assert lib.lbm3_bytes_per_update(lbm.F32) == 216 and lib.lbm3_bytes_per_update(lbm.F64) == 432
+    assert lib.lbm3_bytes_per_update(lbm.F16DEV) == 0
