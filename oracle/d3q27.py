@@ -24,25 +24,48 @@ class _Lat3(C.Structure):
                 ("force", C.c_double * 3)]
 
 
+def _load(path):
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    for name, argc in [("oracle3_velocities", 2), ("oracle3_central_moments", 3),
+                       ("oracle3_from_central_moments", 3), ("oracle3_collide", 4), ("oracle3_source", 3),
+                       ("oracle3_init", 4), ("oracle3_collide_all", 3), ("oracle3_stream_all", 3),
+                       ("oracle3_macros", 4)]:
+        fn = getattr(L, name)
+        fn.argtypes = [vp] * argc
+        fn.restype = None
+    L.oracle3_macros_node.argtypes = [vp, vp, vp, vp]
+    L.oracle3_macros_node.restype = None
+    L.oracle3_equilibrium.argtypes = [C.c_double, vp, vp]
+    L.oracle3_equilibrium.restype = None
+    L.oracle3_run.argtypes = [vp, vp, vp, C.c_long]
+    L.oracle3_run.restype = None
+    return L
+
+
+class substituted_library:
+    """Context manager that routes this module's calls through another build
+    of the D3Q27 oracle source (used to plant mistakes in tests)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(_build.build()["d3q27"])
-        vp = C.c_void_p
-        for name, argc in [("oracle3_velocities", 2), ("oracle3_central_moments", 3),
-                           ("oracle3_from_central_moments", 3), ("oracle3_collide", 4), ("oracle3_source", 3),
-                           ("oracle3_init", 4), ("oracle3_collide_all", 3), ("oracle3_stream_all", 3),
-                           ("oracle3_macros", 4)]:
-            fn = getattr(L, name)
-            fn.argtypes = [vp] * argc
-            fn.restype = None
-        L.oracle3_macros_node.argtypes = [vp, vp, vp, vp]
-        L.oracle3_macros_node.restype = None
-        L.oracle3_equilibrium.argtypes = [C.c_double, vp, vp]
-        L.oracle3_equilibrium.restype = None
-        L.oracle3_run.argtypes = [vp, vp, vp, C.c_long]
-        L.oracle3_run.restype = None
-        _lib = L
+        _lib = _load(_build.build()["d3q27"])
     return _lib
 
 
