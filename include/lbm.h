@@ -122,14 +122,18 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * second population array (ping-pong, allocated by this call; LBM_ENOMEM if
  * it does not fit), runs pairs of steps from even steps and single steps
  * (variant 2 for 16-bit stores, else 0) otherwise, needs a lattice of at
- * least 4 x 4 nodes and is not used while the divergence check is on.
+ * least 4 x 4 nodes and is not used while the divergence check is on;
+ * 4 = variant 3 with two nodes per thread in packed FP32x2 arithmetic (half
+ * the collision's instructions; like variant 1 it may round differently in
+ * the last bit; with stochastic rounding it runs variant 3).
  * The default is 2 for 16-bit stores of at least 2^20 nodes and 0
  * otherwise (a smaller launch is latency-bound and one node per thread is
  * faster).
- * Variants 0, 2 and 3 produce bit-identical states; variant 1 may round
- * differently in the last bit because it fuses multiply-adds explicitly.
- * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
- * variant outside 0..3; a variant the storage kind does not admit selects 0. */
+ * Variants 0, 2 and 3 produce bit-identical states; variants 1 and 4 may
+ * round differently in the last bit because they fuse multiply-adds
+ * explicitly.  With a per-node force field variant 2 runs variant 0.
+ * LBM_EINVAL for a variant outside 0..4; a variant the storage kind does not
+ * admit selects 0. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
@@ -156,11 +160,11 @@ int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
  * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads;
- * variant 3 has one fixed tile) on the lattice itself (the state is snapshot
+ * variants 3 and 4 have one fixed tile) on the lattice itself (the state is snapshot
  * and restored, so it is left unchanged) and keeps the fastest pair; ms (may
- * be NULL) receives the best time per step of variants 0..3 (0 where not run).
+ * be NULL) receives the best time per step of variants 0..4 (0 where not run).
  * Synchronous. */
-int lbm_tune(lbm_t h, int trial_steps, float ms[4]);
+int lbm_tune(lbm_t h, int trial_steps, float ms[5]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own

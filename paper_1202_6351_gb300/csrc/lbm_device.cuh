@@ -406,6 +406,23 @@ LBM_HD double rmul(double a, double b) {
 #endif
 }
 
+// a * b + c as one fused multiply-add in every kernel (not left to the
+// compiler's choice of which of two products to fuse into a sum).
+LBM_HD float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+LBM_HD double fma_rn(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+    return __fma_rn(a, b, c);
+#else
+    return fma(a, b, c);
+#endif
+}
+
 // ---------------------------------------------------------------- moments
 template <typename R>
 struct Moments {
@@ -633,12 +650,15 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
         s8 = R(6) * ((R(3) * uyy - R(2)) * fxux + (R(3) * uxx - R(2)) * fyuy);
     }
     // change of each orthogonal moment divided by its norm D_b
-    const R g3 = (-c.w3 * (m3 - e3) + (R(1) - R(0.5) * c.w3) * s3) * R(1.0 / 36.0);
-    const R g4 = (-c.w4 * (m4 - e4) + (R(1) - R(0.5) * c.w4) * s4) * R(0.25);
-    const R g5 = (-c.w5 * (m5 - e5) + (R(1) - R(0.5) * c.w5) * s5) * R(0.25);
-    const R g6 = (-c.w6 * (m6 - e6) + (R(1) - R(0.5) * c.w6) * s6) * R(1.0 / 12.0);
-    const R g7 = (-c.w7 * (m7 - e7) + (R(1) - R(0.5) * c.w7) * s7) * R(1.0 / 12.0);
-    const R g8 = (-c.w8 * (m8 - e8) + (R(1) - R(0.5) * c.w8) * s8) * R(1.0 / 36.0);
+    // -w (m - m_eq) + (1 - w/2) m_s: the source product rounded on its own, the
+    // relaxation product fused into the sum
+    auto relax = [](R w, R dm, R sm) { return fma_rn(-w, dm, rmul(R(1) - R(0.5) * w, sm)); };
+    const R g3 = relax(c.w3, m3 - e3, s3) * R(1.0 / 36.0);
+    const R g4 = relax(c.w4, m4 - e4, s4) * R(0.25);
+    const R g5 = relax(c.w5, m5 - e5, s5) * R(0.25);
+    const R g6 = relax(c.w6, m6 - e6, s6) * R(1.0 / 12.0);
+    const R g7 = relax(c.w7, m7 - e7, s7) * R(1.0 / 12.0);
+    const R g8 = relax(c.w8, m8 - e8, s8) * R(1.0 / 36.0);
     // d += K g over b = 3..8 with columns of Eq. (3), plus the momentum source F/6 on K1, K2
     R fx6 = 0, fy6 = 0;
     if (FORCED) { fx6 = Fx * R(1.0 / 6.0); fy6 = Fy * R(1.0 / 6.0); }

@@ -55,6 +55,7 @@ __device__ __forceinline__ F2& operator-=(F2& x, P2 p) { return x = x - p; }
 
 __device__ __forceinline__ F2 recip(F2 x) { return F2(make_float2(recip(x.v.x), recip(x.v.y))); }
 __device__ __forceinline__ F2 rmul(F2 a, F2 b) { return F2(a * b); }  // rounded product (P2 -> F2)
+__device__ __forceinline__ F2 fma_rn(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 
 template <>
 __host__ __device__ inline F2 wgt<F2>(int q) { return F2(wgt<float>(q)); }

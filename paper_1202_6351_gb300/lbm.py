@@ -268,8 +268,8 @@ class Lattice:
 
     def tune(self, trial_steps=20):
         """Time the kernel variants and CTA shapes, keep the fastest; returns the
-        best ms per step of variants 0..3 (0.0 where the storage has no such variant)."""
-        ms = (C.c_float * 4)()
+        best ms per step of variants 0..4 (0.0 where the storage has no such variant)."""
+        ms = (C.c_float * 5)()
         _check(self.lib.lbm_tune(self.h, int(trial_steps), ms))
         return tuple(ms)
 

@@ -220,7 +220,7 @@ def stability_thresholds():
     out = {}
     for n in TABLE_IV_GRIDS:
         for model in (lbm.BGK, lbm.RAWMRT, lbm.CASCADED):
-            th, un, _ = X.max_stable_cell_reynolds_refined(model, n, hi=1000.0, first=20)
+            th, un, _ = X.max_stable_cell_reynolds_refined(model, n)
             out[model, n] = (th, un)
             print(f"{n}^2 {lbm.MODEL_NAMES[model]}: stable up to {th:.2f}, unstable at {un}")
     return out
