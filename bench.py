@@ -43,8 +43,11 @@ def parse():
     p.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
     p.add_argument("--no-extras", action="store_true", help="skip the sibling / precision comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--part", choices=["all", "adjoint", "batch"], default="all",
-                   help="adjoint / batch: run only that measurement and print it (for profiling)")
+    p.add_argument("--part", choices=["all", "adjoint", "batch", "cost", "steps"], default="all",
+                   help="adjoint / batch: run only that measurement and print it; cost: four single-launch "
+                        "steps of each collision model in FP32 and FP64 storage on --n^2; steps: --steps "
+                        "steps of the --store lattice in kernel --variant (for profiling)")
+    p.add_argument("--variant", type=int, default=-1, help="kernel variant for --part steps (-1: the default)")
     p.add_argument("--adjoint-n", type=int, default=512)
     p.add_argument("--adjoint-steps", type=int, default=2000)
     p.add_argument("--batch-steps", type=int, default=200)
@@ -860,8 +863,23 @@ def run_part(args):
     peak, _ = measured_peaks()
     if args.part == "adjoint":
         out = run_adjoint_extras(lbm, torch, np, sp, n=args.adjoint_n, steps=args.adjoint_steps, peak=peak)
-    else:
+    elif args.part == "batch":
         out = run_batch_extras(lbm, torch, np, peak, sp, steps=args.batch_steps)
+    else:
+        from paper_1202_6351_gb300 import workloads
+
+        n = args.n
+        rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+        stores = {"f32": lbm.F32, "f16": lbm.F16DEV, "bf16": lbm.BF16DEV, "f64": lbm.F64}
+        runs = ([(m, st, -1, 4) for st in (lbm.F32, lbm.F64) for m in (lbm.CASCADED, lbm.BGK, lbm.RAWMRT)]
+                if args.part == "cost" else [(lbm.CASCADED, stores[args.store], args.variant, args.steps)])
+        for model, st, variant, steps in runs:
+            with lbm.Lattice(n, n, omegas(), model=model, store=st, stream=sp) as L:
+                if variant >= 0:
+                    L.set_variant(variant)
+                L.set_graph_steps(0).init(rho, u).step(steps)
+                torch.cuda.synchronize()
+        out = {"runs": len(runs), "n": n}
     print(json.dumps({"part": args.part, **out}), flush=True)
     return 0
 
