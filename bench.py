@@ -503,7 +503,7 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
             "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10}
     # the per-lattice tuner's timings of the kernel variants on this workload
     names = ("one_node_per_thread_mlups", "two_rows_packed_fp32x2_mlups", "four_nodes_64bit_mlups",
-             "two_steps_per_launch_tma_mlups", "two_steps_per_launch_tma_packed_fp32x2_mlups")
+             "two_steps_per_launch_tma_mlups")
     tuned = {}
     for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV), ("bf16", lbm.BF16DEV)):
         L = make(lbm.CASCADED, st)

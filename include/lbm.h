@@ -122,18 +122,14 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * second population array (ping-pong, allocated by this call; LBM_ENOMEM if
  * it does not fit), runs pairs of steps from even steps and single steps
  * (variant 2 for 16-bit stores, else 0) otherwise, needs a lattice of at
- * least 4 x 4 nodes and is not used while the divergence check is on;
- * 4 = variant 3 with two nodes per thread in packed FP32x2 arithmetic (half
- * the collision's instructions; like variant 1 it may round differently in
- * the last bit; with stochastic rounding it runs variant 3).
+ * least 4 x 4 nodes and is not used while the divergence check is on.
  * The default is 2 for 16-bit stores of at least 2^20 nodes and 0
  * otherwise (a smaller launch is latency-bound and one node per thread is
  * faster).
- * Variants 0, 2 and 3 produce bit-identical states; variants 1 and 4 may
- * round differently in the last bit because they fuse multiply-adds
- * explicitly.  With a per-node force field variant 2 runs variant 0.
- * LBM_EINVAL for a variant outside 0..4; a variant the storage kind does not
- * admit selects 0. */
+ * Variants 0, 2 and 3 produce bit-identical states; variant 1 may round
+ * differently in the last bit because it fuses multiply-adds explicitly.
+ * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
+ * variant outside 0..3; a variant the storage kind does not admit selects 0. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
@@ -160,11 +156,11 @@ int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
  * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads;
- * variants 3 and 4 have one fixed tile) on the lattice itself (the state is snapshot
+ * variant 3 has one fixed tile) on the lattice itself (the state is snapshot
  * and restored, so it is left unchanged) and keeps the fastest pair; ms (may
- * be NULL) receives the best time per step of variants 0..4 (0 where not run).
+ * be NULL) receives the best time per step of variants 0..3 (0 where not run).
  * Synchronous. */
-int lbm_tune(lbm_t h, int trial_steps, float ms[5]);
+int lbm_tune(lbm_t h, int trial_steps, float ms[4]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own
@@ -295,8 +291,9 @@ int lbm_batch_destroy(lbm_batch_t b);
  * 64x4, 32x8 threads per 256-thread CTA, each thread updating one node row or
  * four node rows of the tile), work-list order (lattice by lattice,
  * largest first; or one tile of each lattice in turn) and scheduling policy
- * (round robin, contiguous chunks, dynamic via an atomic counter) and keeps
- * the fastest.  The lattices' states are snapshot and restored, so tuning
+ * (a resident grid walking the list round robin, in contiguous chunks or
+ * dynamically via an atomic counter; or one CTA per tile) and keeps the
+ * fastest.  The lattices' states are snapshot and restored, so tuning
  * leaves them unchanged.  best_ms (may be NULL) receives the time per step. */
 int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms);
 
@@ -309,7 +306,8 @@ int lbm_batch_set_graph_steps(lbm_batch_t b, int steps);
 /* Wait for the batch's queued work. */
 int lbm_batch_sync(lbm_batch_t b);
 
-/* cfg = (tile width, tile height in nodes, policy, order, grid CTAs, tiles); stream
+/* cfg = (tile width, tile height in nodes, policy (0 round robin, 1 chunks,
+ * 2 dynamic, 3 one CTA per tile), order, grid CTAs, tiles); stream
  * receives the batch's cudaStream_t (for timing with events).  Either may be NULL. */
 int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
 

@@ -52,6 +52,8 @@ struct lbm_batch_s {
     int* d_counters = nullptr;
     int ncounters = 0;
     int lbx = 7, rows = 1, policy = lbm::kPolicyRoundRobin, order = 0, grid = 0;
+    int resident = 0;  // grid of the persistent policies: SMs x resident CTAs per SM
+    bool flat = false; // one CTA per tile (grid = tiles) instead of a persistent grid
     int sms = 0;
     int graph_steps = 100;
     cudaGraphExec_t graph = nullptr;
@@ -149,6 +151,10 @@ cudaError_t fill_round_table(lbm_batch_s* b, int count, long long base) {
 
 // kstep: the launch's index in a sequence whose round table has rstride entries per domain.
 cudaError_t launch(lbm_batch_s* b, int flip, int* counter, int rstride, int kstep) {
+    // one CTA per tile: the hardware scheduler hands out the tiles and a CTA
+    // that finishes makes room for the next, so loads of many tiles are in
+    // flight at once; the persistent grid walks the list with resident CTAs
+    b->grid = b->flat ? std::max(1, b->ntiles) : b->resident;
     switch (b->model) {
         case LBM_CASCADED:
             return lbm::launch_batch_cascaded(b->grid, b->d_doms, b->d_tiles, b->ntiles, b->lbx, b->rows, flip, b->policy,
@@ -290,7 +296,8 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rtab, size_t(count) * b->ncounters * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) {
-        b->grid = b->sms * blocks_per_sm(b->model);
+        b->resident = b->sms * blocks_per_sm(b->model);
+        b->grid = b->resident;
         e = upload_tiles(b, b->lbx, b->rows, b->order);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -389,15 +396,17 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
     if (e == cudaSuccess) e = refresh_domains(b);
     float best = 1e30f;
     int best_lbx = b->lbx, best_rows = b->rows, best_policy = b->policy, best_order = b->order;
+    bool best_flat = b->flat;
     for (int rows : kRows) {
       for (int lbx : kShapes) {
         for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
             e = upload_tiles(b, lbx, rows, order);
-            for (int policy = 0; policy < 3 && e == cudaSuccess; ++policy) {
+            for (int policy = 0; policy < 4 && e == cudaSuccess; ++policy) {  // 3: one CTA per tile
                 b->lbx = lbx;
                 b->rows = rows;
                 b->order = order;
-                b->policy = policy;
+                b->flat = policy == 3;
+                b->policy = b->flat ? lbm::kPolicyRoundRobin : policy;
                 for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_single(b, k & 1, k);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
                 for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_single(b, k & 1, k);
@@ -409,8 +418,9 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
                     best = ms;
                     best_lbx = lbx;
                     best_rows = rows;
-                    best_policy = policy;
+                    best_policy = b->policy;
                     best_order = order;
+                    best_flat = b->flat;
                 }
                 if (e == cudaSuccess) e = copy_all(false);  // back to the snapshot for the next candidate
             }
@@ -421,6 +431,7 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
     b->rows = best_rows;
     b->policy = best_policy;
     b->order = best_order;
+    b->flat = best_flat;
     b->tuned_ms = best / trial_steps;
     if (e == cudaSuccess) e = upload_tiles(b, b->lbx, b->rows, b->order);
     if (e == cudaSuccess) e = copy_all(false);
@@ -441,9 +452,9 @@ int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream) {
     if (cfg) {
         cfg[0] = 1 << b->lbx;
         cfg[1] = (lbm::kBatchThreads >> b->lbx) * b->rows;
-        cfg[2] = b->policy;
+        cfg[2] = b->flat ? 3 : b->policy;
         cfg[3] = b->order;
-        cfg[4] = b->grid;
+        cfg[4] = b->flat ? std::max(1, b->ntiles) : b->resident;
         cfg[5] = b->ntiles;
     }
     if (stream) *stream = b->stream;

@@ -99,7 +99,7 @@ using lbm::force_mode;
 // The single-step variant that stands in for variant 3 (two fused steps) where
 // one step is taken alone: four nodes per thread for 16-bit stores, else one.
 int single_variant(const lbm_s* h) {
-    if (h->a.variant < 3) return h->a.variant;
+    if (h->a.variant != 3) return h->a.variant;
     return (h->store == LBM_F16DEV || h->store == LBM_BF16DEV) ? 2 : 0;
 }
 
@@ -172,8 +172,7 @@ cudaError_t encode_map(const lbm_s* h, void* base, CUtensorMap* map) {
 // The fused kernel runs on FP32 and 16-bit storage, lattices of at least 4 x 4
 // nodes and without the divergence check (which needs the state every step).
 bool fused_active(const lbm_s* h) {
-    return (h->a.variant == 3 || h->a.variant == 4) && h->store != LBM_F64 && h->a.nx >= 4 && h->a.ny >= 4 &&
-           h->check_every == 0;
+    return h->a.variant == 3 && h->store != LBM_F64 && h->a.nx >= 4 && h->a.ny >= 4 && h->check_every == 0;
 }
 
 // Second population array, descriptors and error word (first use of variant 3).
@@ -544,27 +543,27 @@ int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed) {
     return LBM_OK;
 }
 
-// Variants the storage kind admits: 0 for FP64; 0, 1, 3 and 4 for FP32; 0-4 for 16-bit.
+// Variants the storage kind admits: 0 for FP64; 0, 1 and 3 for FP32; 0-3 for 16-bit.
 static bool variant_allowed(int store, int v) {
     if (store == LBM_F64) return v == 0;
-    if (store == LBM_F32) return v == 0 || v == 1 || v == 3 || v == 4;
-    return v >= 0 && v <= 4;
+    if (store == LBM_F32) return v == 0 || v == 1 || v == 3;
+    return v >= 0 && v <= 3;
 }
 
 int lbm_set_variant(lbm_t h, int variant) {
     CHECK_HANDLE(h);
-    if (variant < 0 || variant > 4) return fail(LBM_EINVAL, "variant must be 0 .. 4");
+    if (variant < 0 || variant > 3) return fail(LBM_EINVAL, "variant must be 0, 1, 2 or 3");
     const int v = variant_allowed(h->store, variant) ? variant : 0;
-    if (v >= 3) LBM_CUDA(ensure_fused(h), "second population array for fused steps");
+    if (v == 3) LBM_CUDA(ensure_fused(h), "second population array for fused steps");
     h->a.variant = v;
     return LBM_OK;
 }
 
-int lbm_tune(lbm_t h, int trial_steps, float ms[5]) {
+int lbm_tune(lbm_t h, int trial_steps, float ms[4]) {
     CHECK_HANDLE(h);
     if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1");
     const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
-    if (ms) ms[0] = ms[1] = ms[2] = ms[3] = ms[4] = 0.f;
+    if (ms) ms[0] = ms[1] = ms[2] = ms[3] = 0.f;
     static const int widths[4] = {128, 256, 64, 32};  // CTA shapes 128x2, 256x1, 64x4, 32x8
     const int v_prev = h->a.variant;
     // `steps` steps from step h->t as lbm_step takes them without graphs
@@ -589,14 +588,14 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[5]) {
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = 0, best_w = 128;
-    for (int v = 0; v < 5 && e == cudaSuccess; ++v) {
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
         if (!variant_allowed(h->store, v)) continue;
-        if (v >= 3 && (ensure_fused(h) != cudaSuccess || h->check_every != 0)) {
+        if (v == 3 && (ensure_fused(h) != cudaSuccess || h->check_every != 0)) {
             cudaGetLastError();  // no room for the second array: variant 3 is not a candidate
             continue;
         }
         float best_of_v = 1e30f;
-        for (int wi = 0; wi < (v >= 3 ? 1 : 4) && e == cudaSuccess; ++wi) {  // variants 3, 4 have a fixed tile
+        for (int wi = 0; wi < (v == 3 ? 1 : 4) && e == cudaSuccess; ++wi) {  // variant 3 has a fixed tile
             h->a.variant = v;
             h->a.block_x = widths[wi];
             e = run(0, 2);

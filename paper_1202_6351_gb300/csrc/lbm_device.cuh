@@ -384,11 +384,12 @@ __device__ __forceinline__ void node_force(const Args& a, int x, int y, R& Fx, R
 }
 
 // ---------------------------------------------------------------- rounded products
-// A product used by more than one later operation is rounded on its own
-// (rmul): whether the compiler would fuse such a product into one of its
-// additions (an FMA) depends on the surrounding code, so without this two
-// kernels that inline the same collision could round it differently.  With
-// it, every kernel variant rounds every node alike.
+// Which product of a sum of two products the compiler fuses into an FMA, and
+// whether it fuses a product that has several uses, depends on the code
+// around the inlined collision.  So wherever a sum has two inexact products,
+// or a product has several uses, the collisions spell the operations out:
+// rmul (a product rounded on its own) and fma_rn (one fused multiply-add).
+// Every kernel variant then rounds every node alike.
 LBM_HD float rmul(float a, float b) {
 #ifdef __CUDA_ARCH__
     return __fmul_rn(a, b);
@@ -471,19 +472,19 @@ LBM_HD void source(R ux, R uy, R Fx, R Fy, R S[9]) {
     const R m3 = R(6) * (fxux + fyuy);
     const R m4 = R(2) * (fxux - fyuy);
     const R m5 = fxuy + fyux;
-    const R m6 = (R(2) - R(3) * uxx) * Fy - R(6) * fxux * uy;
-    const R m7 = (R(2) - R(3) * uyy) * Fx - R(6) * fyuy * ux;
-    const R m8 = R(6) * ((R(3) * uyy - R(2)) * fxux + (R(3) * uxx - R(2)) * fyuy);
+    const R m6 = fma_rn(fma_rn(R(-3), uxx, R(2)), Fy, R(-6) * rmul(fxux, uy));
+    const R m7 = fma_rn(fma_rn(R(-3), uyy, R(2)), Fx, R(-6) * rmul(fyuy, ux));
+    const R m8 = R(6) * fma_rn(fma_rn(R(3), uyy, R(-2)), fxux, rmul(fma_rn(R(3), uxx, R(-2)), fyuy));
     const R k = R(1.0 / 36.0);
     S[0] = k * (R(4) * (m8 - m3));
     S[1] = k * (R(6) * m1 - m3 + R(9) * m4 + R(6) * m7 - R(2) * m8);
     S[2] = k * (R(6) * m2 - m3 - R(9) * m4 + R(6) * m6 - R(2) * m8);
     S[3] = k * (-R(6) * m1 - m3 + R(9) * m4 - R(6) * m7 - R(2) * m8);
     S[4] = k * (-R(6) * m2 - m3 - R(9) * m4 - R(6) * m6 - R(2) * m8);
-    S[5] = k * (R(6) * (m1 + m2) + R(2) * m3 + R(9) * m5 - R(3) * (m6 + m7) + m8);
-    S[6] = k * (R(6) * (m2 - m1) + R(2) * m3 - R(9) * m5 - R(3) * (m6 - m7) + m8);
-    S[7] = k * (-R(6) * (m1 + m2) + R(2) * m3 + R(9) * m5 + R(3) * (m6 + m7) + m8);
-    S[8] = k * (R(6) * (m1 - m2) + R(2) * m3 - R(9) * m5 + R(3) * (m6 - m7) + m8);
+    S[5] = k * (fma_rn(R(6), m1 + m2, R(2) * m3) + R(9) * m5 - R(3) * (m6 + m7) + m8);
+    S[6] = k * (fma_rn(R(6), m2 - m1, R(2) * m3) - R(9) * m5 - R(3) * (m6 - m7) + m8);
+    S[7] = k * (fma_rn(R(-6), m1 + m2, R(2) * m3) + R(9) * m5 + R(3) * (m6 + m7) + m8);
+    S[8] = k * (fma_rn(R(6), m1 - m2, R(2) * m3) - R(9) * m5 + R(3) * (m6 - m7) + m8);
 }
 
 // Add K . g (Eq. 25; g0 = g1 = g2 = 0) to d.
@@ -548,25 +549,26 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = null
     if (FORCED) {
         const R fxuy = rmul(Fx, uy), fyux = rmul(Fy, ux);
         sxx = R(2) * Fx * ux; syy = R(2) * Fy * uy; sxy = fxuy + fyux;
-        sxxy = Fy * uxx + R(2) * Fx * uxy; sxyy = Fx * uyy + R(2) * Fy * uxy;
+        sxxy = fma_rn(Fy, uxx, R(2) * Fx * uxy); sxyy = fma_rn(Fx, uyy, R(2) * Fy * uxy);
         sxxyy = R(2) * uxy * (fxuy + fyux);
     }
     const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;  // full kappa'_xx, kappa'_yy
     // Eq. (17)-(19)
-    const R g3 = c.c3 * (R(2.0 / 3.0) * m.drho + m.rho * (uxx + uyy) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
+    const R g3 = c.c3 * (fma_rn(m.rho, uxx + uyy, R(2.0 / 3.0) * m.drho) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
     const R g4 = c.c4 * (m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy));
     const R g5 = c.c5 * (m.rho * uxy - m.kxy - R(0.5) * sxy);
     const R A = R(3) * g3 + g4, B = R(3) * g3 - g4;
     // Eq. (20)-(21)
-    const R g6 = c.c6 * (R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy)
-               - R(0.5) * uy * A - R(2) * ux * g5;
-    const R g7 = c.c7 * (R(2) * m.rho * ux * uyy + m.kxyy - R(2) * uy * m.kxy - ux * kyy_t - R(0.5) * sxyy)
-               - R(0.5) * ux * B - R(2) * uy * g5;
+    const R g6 = fma_rn(c.c6, R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy,
+                        R(-0.5) * uy * A) - R(2) * ux * g5;
+    const R g7 = fma_rn(c.c7, R(2) * m.rho * ux * uyy + m.kxyy - R(2) * uy * m.kxy - ux * kyy_t - R(0.5) * sxyy,
+                        R(-0.5) * ux * B) - R(2) * uy * g5;
     // Eq. (22)
-    const R g8 = c.c8 * (R(1.0 / 9.0) * m.drho - m.kxxyy + R(3) * m.rho * uxx * uyy
-                         + R(2) * (ux * m.kxyy + uy * m.kxxy) - uxx * kyy_t - uyy * kxx_t
-                         - R(4) * uxy * m.kxy - R(0.5) * sxxyy)
-               - R(2) * g3 - R(0.5) * (uyy * A + uxx * B) - R(4) * uxy * g5 - R(2) * (uy * g6 + ux * g7);
+    const R G8 = R(1.0 / 9.0) * m.drho - m.kxxyy + R(3) * m.rho * uxx * uyy
+               + R(2) * fma_rn(ux, m.kxyy, rmul(uy, m.kxxy)) - uxx * kyy_t - uyy * kxx_t
+               - R(4) * uxy * m.kxy - R(0.5) * sxxyy;
+    const R g8 = fma_rn(c.c8, G8, R(-2) * g3) - R(0.5) * fma_rn(uyy, A, rmul(uxx, B)) - R(4) * uxy * g5
+               - R(2) * fma_rn(uy, g6, rmul(ux, g7));
     if constexpr (TS) {
         R inc[9];
         kernel_increments(inc, g3, g4, g5, g6, g7, g8);
@@ -603,7 +605,7 @@ LBM_HD void collide_bgk(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullptr) 
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
-        const R deq = wgt<R>(q) * (m.drho + m.rho * (R(3) * eu + R(4.5) * eu * eu - usq));
+        const R deq = wgt<R>(q) * (m.drho + m.rho * (fma_rn(R(4.5) * eu, eu, R(3) * eu) - usq));
         if constexpr (TS) {
             R inc = -w * (d[q] - deq);
             if (FORCED) inc += (R(1) - R(0.5) * w) * S[q];
@@ -627,12 +629,12 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
     const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), usq = uxx + uyy;
     // orthogonal moments of d (the rest-state part w rho0 is added to m_eq's side)
     const R tr = m.kxx + m.kyy;
-    const R m3 = R(3) * tr - R(4) * m.drho;
+    const R m3 = fma_rn(R(3), tr, R(-4) * m.drho);
     const R m4 = m.kxx - m.kyy;
     const R m5 = m.kxy;
-    const R m6 = R(2) * m.jy - R(3) * m.kxxy;
-    const R m7 = R(2) * m.jx - R(3) * m.kxyy;
-    const R m8 = R(9) * m.kxxyy - R(6) * tr + R(4) * m.drho;
+    const R m6 = fma_rn(R(-3), m.kxxy, R(2) * m.jy);
+    const R m7 = fma_rn(R(-3), m.kxyy, R(2) * m.jx);
+    const R m8 = fma_rn(R(9), m.kxxyy, fma_rn(R(-6), tr, R(4) * m.drho));
     // equilibrium moments of f_eq - w rho0
     const R p3 = rmul(R(3) * m.rho, usq);  // shared by e3 and e8
     const R e3 = p3 - R(2) * m.drho;
@@ -645,9 +647,9 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
     if (FORCED) {  // the m^s list before Eq. (14)
         const R fxux = rmul(Fx, ux), fyuy = rmul(Fy, uy), fxuy = rmul(Fx, uy), fyux = rmul(Fy, ux);
         s3 = R(6) * (fxux + fyuy); s4 = R(2) * (fxux - fyuy); s5 = fxuy + fyux;
-        s6 = (R(2) - R(3) * uxx) * Fy - R(6) * fxux * uy;
-        s7 = (R(2) - R(3) * uyy) * Fx - R(6) * fyuy * ux;
-        s8 = R(6) * ((R(3) * uyy - R(2)) * fxux + (R(3) * uxx - R(2)) * fyuy);
+        s6 = fma_rn(fma_rn(R(-3), uxx, R(2)), Fy, R(-6) * rmul(fxux, uy));
+        s7 = fma_rn(fma_rn(R(-3), uyy, R(2)), Fx, R(-6) * rmul(fyuy, ux));
+        s8 = R(6) * fma_rn(fma_rn(R(3), uyy, R(-2)), fxux, rmul(fma_rn(R(3), uxx, R(-2)), fyuy));
     }
     // change of each orthogonal moment divided by its norm D_b
     // -w (m - m_eq) + (1 - w/2) m_s: the source product rounded on its own, the

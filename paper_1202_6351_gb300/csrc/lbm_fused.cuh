@@ -27,27 +27,18 @@
 #include <cuda.h>
 
 #include "lbm_device.cuh"
-#include "lbm_pair.cuh"
 
 namespace lbm {
 
-// Tile geometry and launch shape per storage kind.  PAIR: two nodes per
-// thread and iteration in packed FP32x2 arithmetic (half the collision's
-// instructions, twice the registers, so fewer threads per CTA).
-template <int STORE, bool PAIR = false> struct FusedTile;
-template <> struct FusedTile<LBM_F32, false> {
+// Tile geometry and launch shape per storage kind.
+template <int STORE> struct FusedTile;
+template <> struct FusedTile<LBM_F32> {
     static constexpr int TX = 64, TY = 16, ALIGN = 4, THREADS = 512, MIN_BLOCKS = 2;
 };
-template <> struct FusedTile<LBM_F32, true> {
-    static constexpr int TX = 64, TY = 16, ALIGN = 4, THREADS = 256, MIN_BLOCKS = 2;
-};
-template <> struct FusedTile<LBM_F16DEV, false> {
+template <> struct FusedTile<LBM_F16DEV> {
     static constexpr int TX = 64, TY = 16, ALIGN = 8, THREADS = 256, MIN_BLOCKS = 4;
 };
-template <> struct FusedTile<LBM_F16DEV, true> {
-    static constexpr int TX = 64, TY = 16, ALIGN = 8, THREADS = 256, MIN_BLOCKS = 3;
-};
-template <bool PAIR> struct FusedTile<LBM_BF16DEV, PAIR> : FusedTile<LBM_F16DEV, PAIR> {};
+template <> struct FusedTile<LBM_BF16DEV> : FusedTile<LBM_F16DEV> {};
 
 // Shared-memory geometry of the fused kernel for one storage kind.
 template <int STORE>
@@ -116,17 +107,16 @@ enum : int { kFusedErrTimeout = 1 };
 // [9][ny][nx] with row pitch a.pitch.  With stochastic rounding the hashes of
 // steps t and t + 1 are a.rbase and a.rbase1, or a.rtable[a.tstep] and
 // a.rtable[a.tstep + 1] in a graph replay.
-template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR, bool PAIR = false>
-__global__ void __launch_bounds__(FusedTile<STORE, PAIR>::THREADS, FusedTile<STORE, PAIR>::MIN_BLOCKS)
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+__global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::MIN_BLOCKS)
     fused2_kernel(const __grid_constant__ CUtensorMap map, const Args a, void* __restrict__ out,
                   int* __restrict__ err) {
-    static_assert(!(PAIR && SR), "the packed path rounds to nearest");
     using G = FusedGeom<STORE>;
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     constexpr bool TS = SR && STORE == LBM_F32;
-    constexpr int NT = FusedTile<STORE, PAIR>::THREADS;
+    constexpr int NT = FusedTile<STORE>::THREADS;
     extern __shared__ __align__(1024) unsigned char fused_smem[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int ok;
@@ -180,151 +170,74 @@ __global__ void __launch_bounds__(FusedTile<STORE, PAIR>::THREADS, FusedTile<STO
     const Coef<R> c(a);
     const unsigned rb0 = SR ? (a.rtable ? a.rtable[a.tstep] : a.rbase) : 0u;
     const unsigned rb1 = SR ? (a.rtable ? a.rtable[a.tstep + 1] : a.rbase1) : 0u;
-    if constexpr (PAIR) {
-        // ---- 2. and 3. with two nodes per thread and iteration (k and k + NT)
-        // in packed FP32x2 arithmetic; each node is gathered, decoded,
-        // checked and stored on its own, so only the collision is shared.
-        const Coef<F2> c2 = pair_coef(a);
-        for (int k0 = tid; k0 < G::RW * G::RH; k0 += 2 * NT) {
-            int ry[2], rx[2], gx[2], gy[2];
-            bool ok2[2];
-            float dv[2][9], fx[2] = {0.f, 0.f}, fy[2] = {0.f, 0.f};
+    // ---- 2. step t: collide the grown region in place (AA even step: plain stores)
+    for (int k = tid; k < G::RW * G::RH; k += NT) {
+        const int ry = k / G::RW, rx = k % G::RW;
+        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
+        gx = wrap(gx, a.nx);
+        gy = wrap(gy, a.ny);
+        R d[9], e[9];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = min(k0 + h * NT, G::RW * G::RH - 1);
-                ry[h] = k / G::RW;
-                rx[h] = k % G::RW;
-                gx[h] = x0 - 2 + rx[h];
-                gy[h] = y0 - 2 + ry[h];
-                ok2[h] = k0 + h * NT < G::RW * G::RH && !((!perx && (gx[h] < 0 || gx[h] >= a.nx)) ||
-                                                          (!pery && (gy[h] < 0 || gy[h] >= a.ny)));
-                gx[h] = wrap(gx[h], a.nx);
-                gy[h] = wrap(gy[h], a.ny);
+        for (int q = 0; q < 9; ++q) d[q] = S::dec(Aat(q, ry, rx + G::OFF));
+        R Fx, Fy;
+        node_force<R, FORCE>(a, gx, gy, Fx, Fy);
+        collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
+        const unsigned rn = SR ? round_node(a, rb0, gx, gy) : 0u;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) dv[h][q] = S::dec(Aat(q, ry[h], rx[h] + G::OFF));
-                if (FORCE != 0) node_force<float, FORCE>(a, gx[h], gy[h], fx[h], fy[h]);
-            }
-            F2 d[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) d[q] = F2(make_float2(dv[0][q], dv[1][q]));
-            collide<MODEL, F2, (FORCE != 0)>(d, F2(make_float2(fx[0], fx[1])), F2(make_float2(fy[0], fy[1])), c2);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                if (ok2[0]) Aat(q, ry[0], rx[0] + G::OFF) = S::enc(d[q].v.x);
-                if (ok2[1]) Aat(q, ry[1], rx[1] + G::OFF) = S::enc(d[q].v.y);
-            }
+        for (int q = 0; q < 9; ++q) {
+            const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+            T v;
+            if constexpr (TS) v = round_sr32(d[q], e[q], r);
+            else if constexpr (SR) v = enc_sr<STORE>(d[q], r);
+            else v = S::enc(d[q]);
+            Aat(q, ry, rx + G::OFF) = v;
         }
-        __syncthreads();
-        for (int k0 = tid; k0 < G::SW * G::SH; k0 += 2 * NT) {
-            int sy[2], sx[2], gx[2], gy[2];
-            bool ok2[2];
-            float dv[2][9], fx[2] = {0.f, 0.f}, fy[2] = {0.f, 0.f};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = min(k0 + h * NT, G::SW * G::SH - 1);
-                sy[h] = k / G::SW;
-                sx[h] = k % G::SW;
-                gx[h] = x0 - 1 + sx[h];
-                gy[h] = y0 - 1 + sy[h];
-                ok2[h] = k0 + h * NT < G::SW * G::SH && !((!perx && (gx[h] < 0 || gx[h] >= a.nx)) ||
-                                                          (!pery && (gy[h] < 0 || gy[h] >= a.ny)));
-                gx[h] = wrap(gx[h], a.nx);
-                gy[h] = wrap(gy[h], a.ny);
-                const int ry = sy[h] + 1, rxb = sx[h] + 1 + G::OFF;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const int w = (WALLS && ok2[h]) ? incoming_wall(a, q, gx[h], gy[h]) : -1;
-                    if (w >= 0) dv[h][q] = add_wall_term<float>(a, S::dec(Aat(opp(q), ry, rxb)), q, w);
-                    else dv[h][q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
-                }
-                if (FORCE != 0) node_force<float, FORCE>(a, gx[h], gy[h], fx[h], fy[h]);
-            }
-            F2 d[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) d[q] = F2(make_float2(dv[0][q], dv[1][q]));
-            collide<MODEL, F2, (FORCE != 0)>(d, F2(make_float2(fx[0], fx[1])), F2(make_float2(fy[0], fy[1])), c2);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!ok2[h]) continue;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const float v = h == 0 ? d[q].v.x : d[q].v.y;
-                    const int w = WALLS ? incoming_wall(a, opp(q), gx[h], gy[h]) : -1;
-                    Bat(q, sy[h], sx[h]) = S::enc(w >= 0 ? add_wall_term<float>(a, v, opp(q), w) : v);
-                }
-            }
-        }
-        __syncthreads();
-    } else {
-        // ---- 2. step t: collide the grown region in place (AA even step: plain stores)
-        for (int k = tid; k < G::RW * G::RH; k += NT) {
-            const int ry = k / G::RW, rx = k % G::RW;
-            int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-            if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
-            gx = wrap(gx, a.nx);
-            gy = wrap(gy, a.ny);
-            R d[9], e[9];
-    #pragma unroll
-            for (int q = 0; q < 9; ++q) d[q] = S::dec(Aat(q, ry, rx + G::OFF));
-            R Fx, Fy;
-            node_force<R, FORCE>(a, gx, gy, Fx, Fy);
-            collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
-            const unsigned rn = SR ? round_node(a, rb0, gx, gy) : 0u;
-    #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
-                T v;
-                if constexpr (TS) v = round_sr32(d[q], e[q], r);
-                else if constexpr (SR) v = enc_sr<STORE>(d[q], r);
-                else v = S::enc(d[q]);
-                Aat(q, ry, rx + G::OFF) = v;
-            }
-        }
-        __syncthreads();
-
-        // ---- 3. step t + 1 on the tile grown by one node (AA odd step: pull with
-        // the wall links, wall terms added before the rounding of the store)
-        for (int k = tid; k < G::SW * G::SH; k += NT) {
-            const int sy = k / G::SW, sx = k % G::SW;
-            int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
-            if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
-            gx = wrap(gx, a.nx);
-            gy = wrap(gy, a.ny);
-            const int ry = sy + 1, rxb = sx + 1 + G::OFF;
-            R d[9], e[9];
-    #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
-                if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(opp(q), ry, rxb)), q, w);
-                else d[q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
-            }
-            R Fx, Fy;
-            node_force<R, FORCE>(a, gx, gy, Fx, Fy);
-            collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
-            const unsigned rn = SR ? round_node(a, rb1, gx, gy) : 0u;
-    #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
-                const int w = WALLS ? incoming_wall(a, opp(q), gx, gy) : -1;
-                R v = d[q], ev = TS ? e[q] : R(0);
-                if (w >= 0) {
-                    if constexpr (TS) {
-                        float e2;
-                        v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
-                        ev = e[q] + e2;
-                    } else {
-                        v = add_wall_term<R>(a, d[q], opp(q), w);
-                    }
-                }
-                T o;
-                if constexpr (TS) o = round_sr32(v, ev, r);
-                else if constexpr (SR) o = enc_sr<STORE>(v, r);
-                else o = S::enc(v);
-                Bat(q, sy, sx) = o;
-            }
-        }
-        __syncthreads();
     }
+    __syncthreads();
+
+    // ---- 3. step t + 1 on the tile grown by one node (AA odd step: pull with
+    // the wall links, wall terms added before the rounding of the store)
+    for (int k = tid; k < G::SW * G::SH; k += NT) {
+        const int sy = k / G::SW, sx = k % G::SW;
+        int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
+        if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
+        gx = wrap(gx, a.nx);
+        gy = wrap(gy, a.ny);
+        const int ry = sy + 1, rxb = sx + 1 + G::OFF;
+        R d[9], e[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
+            if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(opp(q), ry, rxb)), q, w);
+            else d[q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
+        }
+        R Fx, Fy;
+        node_force<R, FORCE>(a, gx, gy, Fx, Fy);
+        collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
+        const unsigned rn = SR ? round_node(a, rb1, gx, gy) : 0u;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+            const int w = WALLS ? incoming_wall(a, opp(q), gx, gy) : -1;
+            R v = d[q], ev = TS ? e[q] : R(0);
+            if (w >= 0) {
+                if constexpr (TS) {
+                    float e2;
+                    v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
+                    ev = e[q] + e2;
+                } else {
+                    v = add_wall_term<R>(a, d[q], opp(q), w);
+                }
+            }
+            T o;
+            if constexpr (TS) o = round_sr32(v, ev, r);
+            else if constexpr (SR) o = enc_sr<STORE>(v, r);
+            else o = S::enc(v);
+            Bat(q, sy, sx) = o;
+        }
+    }
+    __syncthreads();
 
     // ---- 4. f(t + 2) of the tile: pull from the second buffer, natural layout
     T* __restrict__ fo = static_cast<T*>(out);
@@ -347,29 +260,25 @@ namespace lbm {
 
 // Launch of the fused kernel for one storage kind (dynamic shared memory set
 // up on first use of each instantiation).
-template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR, bool PAIR>
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
 static cudaError_t launch_fused_one(const CUtensorMap& map, const Args& a, void* out, int* err, cudaStream_t s) {
     using G = FusedGeom<STORE>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<MODEL, STORE, FORCE, WALLS, SR, PAIR>,
+        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<MODEL, STORE, FORCE, WALLS, SR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM));
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const dim3 grid((a.nx + G::TX - 1) / G::TX, (a.ny + G::TY - 1) / G::TY);
-    fused2_kernel<MODEL, STORE, FORCE, WALLS, SR, PAIR>
-        <<<grid, FusedTile<STORE, PAIR>::THREADS, G::SMEM, s>>>(map, a, out, err);
+    fused2_kernel<MODEL, STORE, FORCE, WALLS, SR><<<grid, FusedTile<STORE>::THREADS, G::SMEM, s>>>(map, a, out, err);
     return cudaGetLastError();
 }
 
-// Variant 4 (a.variant == 4) takes the packed path; stochastic rounding runs
-// the one-node path of variant 3.
 template <int MODEL, int STORE, int FORCE, bool WALLS>
 static cudaError_t launch_fused_sr(const CUtensorMap& map, const Args& a, void* out, int* err, cudaStream_t s) {
-    if (a.rseed) return launch_fused_one<MODEL, STORE, FORCE, WALLS, true, false>(map, a, out, err, s);
-    if (a.variant == 4) return launch_fused_one<MODEL, STORE, FORCE, WALLS, false, true>(map, a, out, err, s);
-    return launch_fused_one<MODEL, STORE, FORCE, WALLS, false, false>(map, a, out, err, s);
+    return a.rseed ? launch_fused_one<MODEL, STORE, FORCE, WALLS, true>(map, a, out, err, s)
+                   : launch_fused_one<MODEL, STORE, FORCE, WALLS, false>(map, a, out, err, s);
 }
 
 template <int MODEL, int STORE, int FORCE>

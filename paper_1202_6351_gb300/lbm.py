@@ -268,8 +268,8 @@ class Lattice:
 
     def tune(self, trial_steps=20):
         """Time the kernel variants and CTA shapes, keep the fastest; returns the
-        best ms per step of variants 0..4 (0.0 where the storage has no such variant)."""
-        ms = (C.c_float * 5)()
+        best ms per step of variants 0..3 (0.0 where the storage has no such variant)."""
+        ms = (C.c_float * 4)()
         _check(self.lib.lbm_tune(self.h, int(trial_steps), ms))
         return tuple(ms)
 
@@ -376,7 +376,7 @@ class Lattice:
 class Batch:
     """Many lattices advanced by one persistent launch per step (lbm_batch_*)."""
 
-    POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic"}
+    POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic", 3: "one_cta_per_tile"}
     ORDERS = {0: "largest_first", 1: "interleaved"}
 
     def __init__(self, lattices):

@@ -547,7 +547,7 @@ def test_tune_keeps_state_and_picks_a_variant():
     g = lbm.Lattice(n, n, OMEGAS, store=lbm.F16DEV).init(rho, u).step(3)
     before = g.get_f()
     ms = g.tune(10)
-    assert all(m > 0 for m in ms)  # 16-bit storage admits variants 0..4
+    assert all(m > 0 for m in ms)  # 16-bit storage admits variants 0..3
     np.testing.assert_array_equal(g.get_f(), before)
     assert g.time == 3
     g.close()
@@ -646,34 +646,7 @@ def test_fused_variant_is_rejected_for_fp64_and_tuned_elsewhere():
     g = lbm.Lattice(n, n, OMEGAS, store=lbm.F32).init(rho, u).step(3)
     before = g.get_f()
     ms = g.tune(10)
-    assert ms[0] > 0 and ms[1] > 0 and ms[2] == 0 and ms[3] > 0 and ms[4] > 0  # FP32: variants 0, 1, 3, 4
+    assert ms[0] > 0 and ms[1] > 0 and ms[2] == 0 and ms[3] > 0  # FP32: variants 0, 1, 3
     np.testing.assert_array_equal(g.get_f(), before)
     assert g.time == 3
     g.close()
-
-
-@pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
-@pytest.mark.parametrize("case", [c for c in FUSED_CASES if not c[6]],
-                         ids=[f"{c[0]}x{c[1]}-{c[2]}-{lbm.STORE_NAMES[c[5]]}{'-field' if c[4] else ''}"
-                              for c in FUSED_CASES if not c[6]])
-def test_fused_packed_variant_matches_single_steps_to_rounding(model, case):
-    """Variant 4 takes the fused two steps with two nodes per thread in packed
-    FP32x2 arithmetic; it contracts multiply-adds on its own terms, so it
-    agrees with single steps to the last bits of FP32 (and to the storage
-    rounding for 16-bit stores), not bit for bit."""
-    nx, ny, edges, force, field, store, _ = case
-    e, wu = EDGES[edges]
-    rho, u = workloads.random_fields(71, nx, ny, u_amp=0.03, rho_amp=0.01)
-    ff = workloads.random_force_field(5, nx, ny, 1e-5) if field else None
-    out = []
-    for variant in (0, 4):
-        g = lbm.Lattice(nx, ny, OMEGAS, force=force, edges=e, wall_u=wu, model=model, store=store)
-        g.set_variant(variant).set_graph_steps(8)
-        if ff is not None:
-            g.set_force_field(ff)
-        g.init(rho, u).step(1).step(61)
-        out.append(g.get_f())
-        g.close()
-    w = np.abs(out[0] - 1.0 / 9.0).max()  # size of the deviations
-    tol = 1e-5 if store == lbm.F32 else 2e-2
-    assert np.abs(out[1] - out[0]).max() <= tol * w
