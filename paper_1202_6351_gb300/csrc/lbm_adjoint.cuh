@@ -71,7 +71,7 @@ LBM_HD void collide_cascaded_vjp(const R d[9], R Fx, R Fy, const Coef<R>& c, con
     const R px = m.jx + R(0.5) * Fx, py = m.jy + R(0.5) * Fy;
     const R ux = px * inv, uy = py * inv;
     const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), uxy = rmul(ux, uy);
-    const R r3 = c.rho0 * R(1.0 / 3.0);
+    const R r3 = rmul(c.rho0, R(1.0 / 3.0));
     const R P = rmul(Fx, uy) + rmul(Fy, ux);
     const R sxx = R(2) * Fx * ux, syy = R(2) * Fy * uy, sxy = P;
     const R sxxy = Fy * uxx + R(2) * Fx * uxy, sxyy = Fx * uyy + R(2) * Fy * uxy;
@@ -80,7 +80,7 @@ LBM_HD void collide_cascaded_vjp(const R d[9], R Fx, R Fy, const Coef<R>& c, con
     const R G3 = R(2.0 / 3.0) * m.drho + m.rho * (uxx + uyy) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy);
     const R G4 = m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy);
     const R G5 = m.rho * uxy - m.kxy - R(0.5) * sxy;
-    const R g3 = c.c3 * G3, g4 = c.c4 * G4, g5 = c.c5 * G5;
+    const R g3 = rmul(c.c3, G3), g4 = rmul(c.c4, G4), g5 = rmul(c.c5, G5);
     const R A = R(3) * g3 + g4, B = R(3) * g3 - g4;
     const R G6 = R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy;
     const R g6 = c.c6 * G6 - R(0.5) * uy * A - R(2) * ux * g5;

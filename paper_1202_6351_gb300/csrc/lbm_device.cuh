@@ -543,7 +543,7 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = null
     const R ux = (FORCED ? m.jx + R(0.5) * Fx : m.jx) * inv;   // Eq. (27)
     const R uy = (FORCED ? m.jy + R(0.5) * Fy : m.jy) * inv;
     const R uxx = rmul(ux, ux), uyy = rmul(uy, uy), uxy = rmul(ux, uy);
-    const R r3 = c.rho0 * R(1.0 / 3.0);
+    const R r3 = rmul(c.rho0, R(1.0 / 3.0));
     // raw source moments, Eq. (13)
     R sxx = 0, syy = 0, sxy = 0, sxxy = 0, sxyy = 0, sxxyy = 0;
     if (FORCED) {
@@ -554,9 +554,9 @@ LBM_HD void collide_cascaded(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = null
     }
     const R kxx_t = r3 + m.kxx, kyy_t = r3 + m.kyy;  // full kappa'_xx, kappa'_yy
     // Eq. (17)-(19)
-    const R g3 = c.c3 * (fma_rn(m.rho, uxx + uyy, R(2.0 / 3.0) * m.drho) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
-    const R g4 = c.c4 * (m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy));
-    const R g5 = c.c5 * (m.rho * uxy - m.kxy - R(0.5) * sxy);
+    const R g3 = rmul(c.c3, fma_rn(m.rho, uxx + uyy, R(2.0 / 3.0) * m.drho) - (m.kxx + m.kyy) - R(0.5) * (sxx + syy));
+    const R g4 = rmul(c.c4, m.rho * (uxx - uyy) - (m.kxx - m.kyy) - R(0.5) * (sxx - syy));
+    const R g5 = rmul(c.c5, m.rho * uxy - m.kxy - R(0.5) * sxy);
     const R A = R(3) * g3 + g4, B = R(3) * g3 - g4;
     // Eq. (20)-(21)
     const R g6 = fma_rn(c.c6, R(2) * m.rho * uxx * uy + m.kxxy - R(2) * ux * m.kxy - uy * kxx_t - R(0.5) * sxxy,
@@ -655,15 +655,15 @@ LBM_HD void collide_rawmrt(R d[9], R Fx, R Fy, const Coef<R>& c, R* err = nullpt
     // -w (m - m_eq) + (1 - w/2) m_s: the source product rounded on its own, the
     // relaxation product fused into the sum
     auto relax = [](R w, R dm, R sm) { return fma_rn(-w, dm, rmul(R(1) - R(0.5) * w, sm)); };
-    const R g3 = relax(c.w3, m3 - e3, s3) * R(1.0 / 36.0);
+    const R g3 = rmul(relax(c.w3, m3 - e3, s3), R(1.0 / 36.0));
     const R g4 = relax(c.w4, m4 - e4, s4) * R(0.25);
     const R g5 = relax(c.w5, m5 - e5, s5) * R(0.25);
-    const R g6 = relax(c.w6, m6 - e6, s6) * R(1.0 / 12.0);
-    const R g7 = relax(c.w7, m7 - e7, s7) * R(1.0 / 12.0);
-    const R g8 = relax(c.w8, m8 - e8, s8) * R(1.0 / 36.0);
+    const R g6 = rmul(relax(c.w6, m6 - e6, s6), R(1.0 / 12.0));
+    const R g7 = rmul(relax(c.w7, m7 - e7, s7), R(1.0 / 12.0));
+    const R g8 = rmul(relax(c.w8, m8 - e8, s8), R(1.0 / 36.0));
     // d += K g over b = 3..8 with columns of Eq. (3), plus the momentum source F/6 on K1, K2
     R fx6 = 0, fy6 = 0;
-    if (FORCED) { fx6 = Fx * R(1.0 / 6.0); fy6 = Fy * R(1.0 / 6.0); }
+    if (FORCED) { fx6 = rmul(Fx, R(1.0 / 6.0)); fy6 = rmul(Fy, R(1.0 / 6.0)); }
     if constexpr (TS) {
         R inc[9];
         inc[0] = R(-4) * g3 + R(4) * g8;

@@ -76,3 +76,10 @@ def test_both_arms_describe_the_same_workload():
     c = bench.workload_config(4096, "f32")
     assert c["workload"] == "taylor_green_4096x4096_cascaded_f32_store" and c["nodes"] == 4096 ** 2
     assert [k for k, _ in bench.CPU_SAMPLES].count("cavity") == 1
+
+
+def test_launch_count_of_fused_and_single_steps():
+    assert bench.launch_count(0, 20, False) == 20
+    assert bench.launch_count(0, 20, True) == 10
+    assert bench.launch_count(5, 20, True) == 11  # one single step, nine pairs, one single step
+    assert bench.launch_count(1, 1, True) == 1
