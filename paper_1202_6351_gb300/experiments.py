@@ -455,10 +455,65 @@ def matrix_summary(results):
     return out
 
 
+def taylor_green_decay(n, store=lbm.F32, rounding=lbm.ROUND_NEAREST, omega=1.6, fractions=(0.25, 0.5, 1.0),
+                       seed=2026, progress=None):
+    """The Taylor-Green configuration (Sec. III-B) on n^2 (diffusive scaling
+    U0 = 0.04 * 64 / n, shear omega, other rates 1) run to one decay time
+    T = 1 / (2 nu k^2), with the relative L2 velocity error against the
+    analytic decay and the fitted amplitude at the given fractions of T.
+    Returns [(steps, error, amplitude, seconds)]."""
+    import time
+
+    from . import workloads
+
+    nu = (1.0 / omega - 0.5) / 3.0
+    u0 = workloads.diffusive_u0(n)
+    T = workloads.taylor_green_decay_steps(n, nu)
+    rho, u = workloads.taylor_green_init(n, u0)
+    out = []
+    t0 = time.time()
+    with lbm.Lattice(n, n, (1.0, omega, omega, 1.0, 1.0, 1.0), store=store) as L:
+        if rounding == lbm.ROUND_STOCHASTIC:
+            L.set_rounding(rounding, seed)
+        L.init(rho, u)
+        done = 0
+        for fr in fractions:
+            target = int(round(fr * T))
+            L.step(target - done)
+            done = target
+            _, ug = L.macros()
+            ua = workloads.taylor_green_velocity(n, u0, nu, done)
+            err = float(np.sqrt(((ug - ua) ** 2).sum() / (ua ** 2).sum()))
+            amp = float((ug * ua).sum() / (ua * ua).sum())
+            out.append((done, err, amp, time.time() - t0))
+            if progress:
+                progress(out[-1])
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
+    import sys
     import time
+
+    if len(sys.argv) > 1 and sys.argv[1] == "decay":
+        ap = argparse.ArgumentParser(description="Taylor-Green to one decay time on the GPU.")
+        ap.add_argument("decay")
+        ap.add_argument("--n", type=int, default=4096)
+        ap.add_argument("--store", choices=["f32", "f16", "bf16"], default="f32")
+        ap.add_argument("--rounding", choices=["nearest", "stochastic"], default="nearest")
+        args = ap.parse_args()
+        st = {"f32": lbm.F32, "f16": lbm.F16DEV, "bf16": lbm.BF16DEV}[args.store]
+        rd = lbm.ROUND_STOCHASTIC if args.rounding == "stochastic" else lbm.ROUND_NEAREST
+
+        def show(r):
+            print(json.dumps({"n": args.n, "store": args.store, "rounding": args.rounding, "steps": r[0],
+                              "rel_l2_velocity_error": r[1], "amplitude": r[2], "seconds": round(r[3], 1)}),
+                  flush=True)
+
+        taylor_green_decay(args.n, st, rd, progress=show)
+        sys.exit(0)
 
     ap = argparse.ArgumentParser(description="Run the lid-driven cavity matrix (three models, FP32 / FP16) on the GPU.")
     ap.add_argument("--n", type=int, default=257)
