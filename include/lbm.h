@@ -123,13 +123,20 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * it does not fit), runs pairs of steps from even steps and single steps
  * (variant 2 for 16-bit stores, else 0) otherwise, needs a lattice of at
  * least 4 x 4 nodes and is not used while the divergence check is on.
+ * 4 (LBM_F32, LBM_BF16DEV, LBM_F16DEV; lattices without walls) = one step per
+ * launch on a persistent grid that walks the rows in segments of 1024
+ * nodes: bulk asynchronous copies bring a segment's nine population planes
+ * into shared memory several segments ahead, the nodes are collided there
+ * and the segment goes back by bulk stores, so the loads in flight do not
+ * occupy registers.  Walled lattices run variant 2 (16-bit) or 0 instead,
+ * and FP32 with stochastic rounding runs variant 0.
  * The default is 2 for 16-bit stores of at least 2^20 nodes and 0
  * otherwise (a smaller launch is latency-bound and one node per thread is
  * faster).
- * Variants 0, 2 and 3 produce bit-identical states; variant 1 may round
+ * Variants 0, 2, 3 and 4 produce bit-identical states; variant 1 may round
  * differently in the last bit because it fuses multiply-adds explicitly.
  * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
- * variant outside 0..3; a variant the storage kind does not admit selects 0. */
+ * variant outside 0..4; a variant the storage kind does not admit selects 0. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
@@ -155,12 +162,13 @@ int lbm_set_variant(lbm_t h, int variant);
 int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
- * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads;
- * variant 3 has one fixed tile) on the lattice itself (the state is snapshot
- * and restored, so it is left unchanged) and keeps the fastest pair; ms (may
- * be NULL) receives the best time per step of variants 0..3 (0 where not run).
- * Synchronous. */
-int lbm_tune(lbm_t h, int trial_steps, float ms[4]);
+ * the storage and edges admit with each CTA shape (128x2, 256x1, 64x4, 32x8
+ * threads; variants 3 and 4 have one fixed shape) on the lattice itself (the
+ * state is snapshot and restored, so it is left unchanged) and keeps the
+ * fastest pair; ms (may be NULL) receives the best time per step of variants
+ * 0..4 (0 where not run).  Synchronous. */
+#define LBM_NUM_VARIANTS 5
+int lbm_tune(lbm_t h, int trial_steps, float ms[LBM_NUM_VARIANTS]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
  * on_device selects a device or a host pointer.  The library keeps its own
@@ -334,10 +342,9 @@ int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
  * to be cleared.  Calls that overlap on the GPU (concurrent streams or host
  * threads) race on the array and must be serialised by the caller.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The address is kept per device and looked up
- * again by the first call after the device's context has been replaced (for
- * example by cudaDeviceReset).  Allocates nothing.  Errors: LBM_EINVAL (NULL
+ * (cudaGetSymbolAddress, with that device current).  The address is kept per
+ * device and looked up again by the first call after the device's context has
+ * been replaced (for example by cudaDeviceReset).  Allocates nothing.  Errors: LBM_EINVAL (NULL
  * pointer, sizes, pitch < nx, unknown store or edge kind, one edge of an
  * opposite pair periodic and the other a wall), LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_ROWS 16384
