@@ -59,12 +59,16 @@ def omegas():
 
 
 STEP_KERNEL_SOURCES = ("include/lbm.h", "paper_1202_6351_gb300/csrc/lbm_device.cuh",
-                       "paper_1202_6351_gb300/csrc/lbm_fused.cuh",
+                       "paper_1202_6351_gb300/csrc/lbm_fused.cuh", "paper_1202_6351_gb300/csrc/lbm_async.cuh",
                        "paper_1202_6351_gb300/csrc/lbm_internal.h", "paper_1202_6351_gb300/csrc/lbm_pair.cuh",
                        "paper_1202_6351_gb300/csrc/lbm_vec.cuh",
                        "paper_1202_6351_gb300/csrc/lbm_step_impl.cuh", "paper_1202_6351_gb300/csrc/lbm_step_f64.cu",
                        "paper_1202_6351_gb300/csrc/lbm_step_f32.cu", "paper_1202_6351_gb300/csrc/lbm_step_bf16.cu",
                        "paper_1202_6351_gb300/csrc/lbm_step_f16.cu")
+
+
+KERNEL_NAMES = {2: "step_kernel_vec (one step per launch, four nodes per thread)",
+                3: "fused2_kernel (two steps per launch)"}
 
 
 def strip_comments(text: str) -> str:
@@ -422,7 +426,11 @@ def run_ours(args):
     sampler = ClockSampler(uuid) if rank == 0 else None
     if sampler:
         sampler.wait_first()
-    L.step(args.warmup)
+    # W warm-up steps, one more if W is odd and the kernel takes steps in pairs:
+    # a pair of steps starts at an even step, so a pass that started at an odd
+    # step would time two single-step launches at its ends
+    warmup_run = args.warmup + (1 if variant == 3 and args.warmup % 2 else 0)
+    L.step(warmup_run)
     first, w0, _ = timed(L, args.steps)
     passes = passes_for(first, dist)
     pass_secs = [first] + [timed(L, args.steps)[0] for _ in range(passes - 1)]
@@ -444,13 +452,13 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_update": bpu,
                 "algorithmic_bytes_per_launch": bpu * nodes * updates_per_launch,
-                "kernel": "fused2_kernel (two steps per launch)" if two_step else "step_kernel (one step per launch)"}
+                "kernel": KERNEL_NAMES.get(variant, "step_kernel (one step per launch)")}
     if two_step:
         # one read and one write of the state per two steps: the design's own
         # DRAM bytes per update are half of the per-step algorithmic bytes
         roofline["design_bytes_per_update"] = bpu // 2
         roofline["frac_of_design_bytes"] = round(achieved / 2 / peak, 4)
-    launches = launch_count(args.warmup, args.steps, two_step)
+    launches = launch_count(warmup_run, args.steps, two_step)
     L.close()
 
     # ---- end to end through the C ABI with pinned host buffers (every rank, right
@@ -484,7 +492,8 @@ def run_ours(args):
                        "reported": "median pass of K steps (max over ranks); every pass is K steps bracketed by "
                                    "barrier + synchronize, timed with CUDA events on the launching stream",
                        "timed_window_s": round(w1 - w0, 3), "gpu_launches_all_passes": launches * len(pass_secs),
-                       "kernel_variant": variant, "tuned_ms_per_step": round(tuned_ms[variant], 5)},
+                       "kernel_variant": variant, "tuned_ms_per_step": round(tuned_ms[variant], 5),
+                       "warmup_steps_run": warmup_run},
             "clocks": clocks,
             "e2e": e2e,
             "extras": extras,
@@ -518,6 +527,9 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
         L = make(lbm.CASCADED, st)
         if rounding == lbm.ROUND_STOCHASTIC:
             L.set_rounding(rounding, 2026)
+        if st != lbm.F32:  # 16-bit: the tuner's variant; FP32 stays on one node per thread (variant 0)
+            L.tune(50)
+        variant = L.info()["variant"]
         L.step(10)
         s, _, _ = timed(L, steps)
         _, u = L.macros()
@@ -526,7 +538,7 @@ def run_extras(args, make, timed, lbm, nodes, peak, np):
         out[f"cascaded_{name}"] = {
             "mlups": round(nodes * steps / s / 1e6, 1),
             "frac": round(lbm.lbm_bytes_per_update(st) * nodes * steps / s / 1e9 / peak, 4),
-            "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10}
+            "rel_l2_velocity_error_vs_f64": err, "after_steps": steps + 10, "variant": variant}
     # the per-lattice tuner's timings of the kernel variants on this workload
     names = ("one_node_per_thread_mlups", "two_rows_packed_fp32x2_mlups", "four_nodes_64bit_mlups",
              "two_steps_per_launch_tma_mlups")

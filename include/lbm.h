@@ -123,20 +123,13 @@ int lbm_set_omegas(lbm_t h, const double omegas[6]);
  * it does not fit), runs pairs of steps from even steps and single steps
  * (variant 2 for 16-bit stores, else 0) otherwise, needs a lattice of at
  * least 4 x 4 nodes and is not used while the divergence check is on.
- * 4 (LBM_F32, LBM_BF16DEV, LBM_F16DEV; lattices without walls) = one step per
- * launch on a persistent grid that walks the rows in segments of 1024
- * nodes: bulk asynchronous copies bring a segment's nine population planes
- * into shared memory several segments ahead, the nodes are collided there
- * and the segment goes back by bulk stores, so the loads in flight do not
- * occupy registers.  Walled lattices run variant 2 (16-bit) or 0 instead,
- * and FP32 with stochastic rounding runs variant 0.
  * The default is 2 for 16-bit stores of at least 2^20 nodes and 0
  * otherwise (a smaller launch is latency-bound and one node per thread is
  * faster).
- * Variants 0, 2, 3 and 4 produce bit-identical states; variant 1 may round
+ * Variants 0, 2 and 3 produce bit-identical states; variant 1 may round
  * differently in the last bit because it fuses multiply-adds explicitly.
  * With a per-node force field variant 2 runs variant 0.  LBM_EINVAL for a
- * variant outside 0..4; a variant the storage kind does not admit selects 0. */
+ * variant outside 0..3; a variant the storage kind does not admit selects 0. */
 int lbm_set_variant(lbm_t h, int variant);
 
 /* Rounding of the stored deviations (LBM_F32, LBM_BF16DEV, LBM_F16DEV).
@@ -162,12 +155,12 @@ int lbm_set_variant(lbm_t h, int variant);
 int lbm_set_rounding(lbm_t h, int mode, unsigned long long seed);
 
 /* Autotuner for one lattice: times `trial_steps` steps of each kernel variant
- * the storage and edges admit with each CTA shape (128x2, 256x1, 64x4, 32x8
- * threads; variants 3 and 4 have one fixed shape) on the lattice itself (the
- * state is snapshot and restored, so it is left unchanged) and keeps the
- * fastest pair; ms (may be NULL) receives the best time per step of variants
- * 0..4 (0 where not run).  Synchronous. */
-#define LBM_NUM_VARIANTS 5
+ * the storage admits with each CTA shape (128x2, 256x1, 64x4, 32x8 threads;
+ * variant 3 has one fixed tile) on the lattice itself (the state is snapshot
+ * and restored, so it is left unchanged) and keeps the fastest pair; ms (may
+ * be NULL) receives the best time per step of variants 0..3 (0 where not run).
+ * Synchronous. */
+#define LBM_NUM_VARIANTS 4
 int lbm_tune(lbm_t h, int trial_steps, float ms[LBM_NUM_VARIANTS]);
 
 /* Per-node body force [2][ny][nx] added to the uniform force; NULL removes it.
@@ -300,9 +293,11 @@ int lbm_batch_destroy(lbm_batch_t b);
  * four node rows of the tile), work-list order (lattice by lattice,
  * largest first; or one tile of each lattice in turn) and scheduling policy
  * (a resident grid walking the list round robin, in contiguous chunks or
- * dynamically via an atomic counter; or one CTA per tile) and keeps the
- * fastest.  The lattices' states are snapshot and restored, so tuning
- * leaves them unchanged.  best_ms (may be NULL) receives the time per step. */
+ * dynamically via an atomic counter; or one CTA per tile), and, where every
+ * lattice admits it and all are at the same even step, two steps per launch
+ * (lbm_batch_set_two_step); keeps the fastest.  The lattices' states are
+ * snapshot and restored, so tuning leaves them unchanged.  best_ms (may be
+ * NULL) receives the time per step. */
 int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms);
 
 /* Advance every lattice of the batch by n >= 0 steps (asynchronous). */
@@ -311,11 +306,25 @@ int lbm_batch_step(lbm_batch_t b, long n);
 /* Steps per CUDA graph (even, 0..4096; 0 disables graphs). */
 int lbm_batch_set_graph_steps(lbm_batch_t b, int steps);
 
-/* Wait for the batch's queued work. */
+/* Wait for the batch's queued work.  LBM_ECUDA also if a two-step launch
+ * timed out waiting for its tile load (the states are then invalid). */
 int lbm_batch_sync(lbm_batch_t b);
 
+/* Two steps per launch for the whole batch (on != 0): one CTA per 64 x 16
+ * tile of any lattice takes both steps of the tile in shared memory (the tile
+ * body of lbm_set_variant's variant 3, with its storage kind, edges, force and
+ * rounding), so the populations cross HBM once per two steps.  Every lattice
+ * gets a second population array (allocated here, kept by the lattice) and
+ * the arrays trade roles at every launch.  lbm_batch_step then takes pairs of
+ * steps from even steps and single batched steps for an odd start or end; a
+ * call whose lattices are at steps of different parity takes single steps
+ * only.  Results are bit for bit those of single steps.  Errors: LBM_EINVAL
+ * (a lattice smaller than 4 x 4 nodes), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_set_two_step(lbm_batch_t b, int on);
+
 /* cfg = (tile width, tile height in nodes, policy (0 round robin, 1 chunks,
- * 2 dynamic, 3 one CTA per tile), order, grid CTAs, tiles); stream
+ * 2 dynamic, 3 one CTA per tile, 4 two steps per launch, one CTA per tile),
+ * order, grid CTAs, tiles); stream
  * receives the batch's cudaStream_t (for timing with events).  Either may be NULL. */
 int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream);
 

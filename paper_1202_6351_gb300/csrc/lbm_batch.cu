@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_batch_fused.cuh"
 #include "lbm_batch_impl.cuh"
 #include "lbm_handle.h"
 
@@ -17,6 +18,12 @@ cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int,
                              cudaStream_t);
 cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int, int*, const unsigned*, int,
                                 int, cudaStream_t);
+cudaError_t launch_batch_fused_cascaded(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
+                                        int, int*, cudaStream_t);
+cudaError_t launch_batch_fused_bgk(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int, int,
+                                   int*, cudaStream_t);
+cudaError_t launch_batch_fused_rawmrt(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
+                                      int, int*, cudaStream_t);
 
 // rtab[d * rstride + k] = the hash of (seed, t + base + k) of domain d, for the
 // k-th launch of a sequence that starts `base` steps after the domains' counts t.
@@ -62,6 +69,17 @@ struct lbm_batch_s {
     // a graph replay or a single launch, [doms][ncounters], filled before each.
     unsigned* d_rtab = nullptr;
     bool any_sr = false;
+    // Two steps per launch (lbm_batch_set_two_step, or chosen by the tuner):
+    // every lattice's two arrays and their tensor maps (pinned staging and
+    // device copy), the list of 64 x 16 tiles, the kernels' error word and a
+    // graph of two-step launches.
+    bool two_step = false;
+    lbm::BatchPair* h_pairs = nullptr;
+    lbm::BatchPair* d_pairs = nullptr;
+    int* d_tiles2 = nullptr;
+    int ntiles2 = 0;
+    int* d_err = nullptr;
+    cudaGraphExec_t graph2 = nullptr;
 };
 
 namespace {
@@ -119,10 +137,24 @@ cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int rows, int order) {
     return cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
 }
 
-// Copies each domain's current arguments and parity into the device table.
+// Copies each domain's current arguments and parity into the device table
+// (and, once two-step launches are prepared, each lattice's arrays and maps).
 cudaError_t refresh_domains(lbm_batch_s* b) {
     cudaError_t e = cudaEventSynchronize(b->done);  // the previous upload has finished reading h_doms
     if (e != cudaSuccess) return e;
+    if (b->h_pairs) {
+        for (size_t i = 0; i < b->doms.size(); ++i) {
+            const lbm_s* h = b->doms[i];
+            lbm::BatchPair& P = b->h_pairs[i];
+            P.arr[0] = h->state;
+            P.arr[1] = h->state_alt;
+            P.map[0] = lbm_tensor_map(h, h->state);
+            P.map[1] = lbm_tensor_map(h, h->state_alt);
+        }
+        e = cudaMemcpyAsync(b->d_pairs, b->h_pairs, b->doms.size() * sizeof(lbm::BatchPair), cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e != cudaSuccess) return e;
+    }
     bool any_sr = false;
     for (size_t i = 0; i < b->doms.size(); ++i) {
         const lbm_s* h = b->doms[i];
@@ -180,6 +212,122 @@ cudaError_t launch_single(lbm_batch_s* b, int flip, long long base) {
 void drop_graph(lbm_batch_s* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->graph2) cudaGraphExecDestroy(b->graph2);
+    b->graph2 = nullptr;
+}
+
+// ---------------------------------------------------------------- two steps per launch
+// Every lattice admits two-step launches if it has at least 4 x 4 nodes (the
+// storage kinds of a batch all do); a sequence of them needs every lattice at
+// an even step, so a call whose lattices differ in parity takes single steps.
+bool two_step_admitted(const lbm_batch_s* b) {
+    for (const lbm_s* h : b->doms)
+        if (h->a.nx < 4 || h->a.ny < 4) return false;
+    return true;
+}
+
+bool same_parity(const lbm_batch_s* b) {
+    for (const lbm_s* h : b->doms)
+        if ((h->t & 1) != (b->doms[0]->t & 1)) return false;
+    return true;
+}
+
+// Second arrays and tensor maps of every lattice, the 64 x 16 tile list (largest
+// lattice first) and the error word; made once.
+cudaError_t prepare_two_step(lbm_batch_s* b) {
+    if (b->h_pairs) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (lbm_s* h : b->doms)
+        if (e == cudaSuccess) e = lbm_prepare_two_step(h);
+    std::vector<int> idx(b->doms.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
+        return (long long)b->doms[p]->a.nx * b->doms[p]->a.ny > (long long)b->doms[q]->a.nx * b->doms[q]->a.ny;
+    });
+    std::vector<int> t;
+    for (int d : idx) {
+        const int tx = (b->doms[d]->a.nx + lbm::kBatchFusedTX - 1) / lbm::kBatchFusedTX;
+        const int ty = (b->doms[d]->a.ny + lbm::kBatchFusedTY - 1) / lbm::kBatchFusedTY;
+        for (int j = 0; j < ty; ++j)
+            for (int i = 0; i < tx; ++i) t.insert(t.end(), {d, i, j});
+    }
+    lbm::BatchPair* hp = nullptr;
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&hp, b->doms.size() * sizeof(lbm::BatchPair));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_pairs, b->doms.size() * sizeof(lbm::BatchPair));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles2, t.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tiles2, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // t is a local vector
+    if (e != cudaSuccess) {
+        if (hp) cudaFreeHost(hp);
+        return e;
+    }
+    b->ntiles2 = int(t.size() / 3);
+    b->h_pairs = hp;
+    return cudaSuccess;
+}
+
+// Two-step launch k of a sequence (reads each lattice's arr[k & 1]); the round
+// table holds rstride hashes per lattice, two per launch from 2 kstep.
+cudaError_t launch_pair(lbm_batch_s* b, int k, int rstride, int kstep) {
+    switch (b->model) {
+        case LBM_CASCADED:
+            return lbm::launch_batch_fused_cascaded(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride,
+                                                    kstep, b->d_err, b->stream);
+        case LBM_BGK:
+            return lbm::launch_batch_fused_bgk(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride, kstep,
+                                               b->d_err, b->stream);
+        default:
+            return lbm::launch_batch_fused_rawmrt(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride,
+                                                  kstep, b->d_err, b->stream);
+    }
+}
+
+// Launches per replay of the two-step graph: graph_steps / 2, rounded down to an
+// even number (the arrays are back in place after each replay).
+int pair_graph_len(const lbm_batch_s* b) { return (b->graph_steps / 4) * 2; }
+
+cudaError_t build_graph2(lbm_batch_s* b) {
+    if (b->graph2) cudaGraphExecDestroy(b->graph2);
+    b->graph2 = nullptr;
+    const int len = pair_graph_len(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < len && e == cudaSuccess; ++k) e = launch_pair(b, k & 1, 2 * len, k);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph2, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// `pairs` two-step launches from the domains' current steps plus `base` (all
+// even); the lattices' arrays trade roles if pairs is odd.
+cudaError_t run_pairs(lbm_batch_s* b, long pairs, long long base) {
+    cudaError_t e = cudaSuccess;
+    long p = 0;
+    const int len = pair_graph_len(b);
+    if (len > 0 && pairs >= len) {
+        if (!b->graph2) e = build_graph2(b);
+        for (; e == cudaSuccess && pairs - p >= len; p += len) {
+            e = fill_round_table(b, 2 * len, base + 2 * p);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->graph2, b->stream);
+        }
+    }
+    for (; e == cudaSuccess && p < pairs; ++p) {
+        e = fill_round_table(b, 2, base + 2 * p);
+        if (e == cudaSuccess) e = launch_pair(b, int(p & 1), 2, 0);
+    }
+    if (e == cudaSuccess && (pairs & 1)) {
+        for (lbm_s* h : b->doms) {
+            std::swap(h->state, h->state_alt);
+            h->a.f = h->state;
+        }
+    }
+    return e;
 }
 
 cudaError_t build_graph(lbm_batch_s* b) {
@@ -316,6 +464,10 @@ int lbm_batch_destroy(lbm_batch_t b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_pairs) cudaFreeHost(b->h_pairs);
+    if (b->d_pairs) cudaFree(b->d_pairs);
+    if (b->d_tiles2) cudaFree(b->d_tiles2);
+    if (b->d_err) cudaFree(b->d_err);
     if (b->d_rtab) cudaFree(b->d_rtab);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_doms) cudaFree(b->d_doms);
@@ -346,6 +498,25 @@ int lbm_batch_step(lbm_batch_t b, long n) {
         if (h->has_field) return fail(LBM_EINVAL, "lbm_batch_step: a lattice now has a per-node force field");
     BATCH_CUDA(wait_for_domains(b), "lbm_batch_step: waiting for the lattices' streams");
     BATCH_CUDA(refresh_domains(b), "lbm_batch_step: domain table");
+    if (b->two_step && same_parity(b)) {  // [one step to an even step,] pairs of steps[, one step]
+        long done = 0;
+        if (b->doms[0]->t & 1) {
+            BATCH_CUDA(launch_single(b, 0, 0), "lbm_batch_step: launch");
+            done = 1;
+        }
+        const long pairs = (n - done) / 2;
+        BATCH_CUDA(run_pairs(b, pairs, done), "lbm_batch_step: two-step launches");
+        for (lbm_s* h : b->doms) h->t += done + 2 * pairs;
+        if (done + 2 * pairs < n) {  // the arrays may have traded roles: a fresh table for the last step
+            BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_step: sync");
+            BATCH_CUDA(cudaEventRecord(b->done, b->stream), "lbm_batch_step: event");
+            BATCH_CUDA(refresh_domains(b), "lbm_batch_step: domain table");
+            BATCH_CUDA(launch_single(b, 0, 0), "lbm_batch_step: launch");
+            for (lbm_s* h : b->doms) h->t += 1;
+        }
+        BATCH_CUDA(release_domains(b), "lbm_batch_step: event");
+        return LBM_OK;
+    }
     long done = 0;
     if (b->graph_steps > 0 && n >= b->graph_steps) {
         if (!b->graph) BATCH_CUDA(build_graph(b), "lbm_batch_step: graph capture");
@@ -364,6 +535,25 @@ int lbm_batch_sync(lbm_batch_t b) {
     if (!b) return fail(LBM_EINVAL, "null batch");
     Guard g(b->device);
     BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_sync");
+    if (b->d_err) {  // a two-step launch whose tile load timed out (cleared once reported)
+        int v = 0;
+        BATCH_CUDA(cudaMemcpy(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "lbm_batch_sync: error word");
+        if (v) {
+            cudaMemset(b->d_err, 0, sizeof(int));
+            return fail(LBM_ECUDA, "lbm_batch_sync: a two-step launch timed out waiting for its tile load");
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_set_two_step(lbm_batch_t b, int on) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    Guard g(b->device);
+    if (on && !two_step_admitted(b))
+        return fail(LBM_EINVAL, "lbm_batch_set_two_step: every lattice needs at least 4 x 4 nodes");
+    BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_set_two_step");
+    if (on) BATCH_CUDA(prepare_two_step(b), "lbm_batch_set_two_step: second arrays");
+    b->two_step = on != 0;
     return LBM_OK;
 }
 
@@ -427,12 +617,40 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
         }
       }
     }
+    // two steps per launch: an even number of launches, so the states end in
+    // the arrays they started from
+    bool best_two = false;
+    float best_step = best / trial_steps;
+    if (e == cudaSuccess && two_step_admitted(b) && same_parity(b) && (b->doms[0]->t & 1) == 0) {
+        if (prepare_two_step(b) != cudaSuccess) {
+            cudaGetLastError();  // no room for the second arrays: not a candidate
+        } else {
+            const int launches = std::max(2, ((trial_steps + 1) / 2 + 1) & ~1);
+            e = cudaStreamSynchronize(b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
+            if (e == cudaSuccess) e = refresh_domains(b);
+            if (e == cudaSuccess) e = fill_round_table(b, 2, 0);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_pair(b, k & 1, 2, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+            for (int k = 0; k < launches && e == cudaSuccess; ++k) e = launch_pair(b, k & 1, 2, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && ms / (2 * launches) < best_step) {
+                best_step = ms / (2 * launches);
+                best_two = true;
+            }
+            if (e == cudaSuccess) e = copy_all(false);
+        }
+    }
+    b->two_step = best_two;
     b->lbx = best_lbx;
     b->rows = best_rows;
     b->policy = best_policy;
     b->order = best_order;
     b->flat = best_flat;
-    b->tuned_ms = best / trial_steps;
+    b->tuned_ms = best_step;
     if (e == cudaSuccess) e = upload_tiles(b, b->lbx, b->rows, b->order);
     if (e == cudaSuccess) e = copy_all(false);
     cudaFreeAsync(backup, b->stream);
@@ -449,7 +667,14 @@ int lbm_batch_tune(lbm_batch_t b, int trial_steps, float* best_ms) {
 
 int lbm_batch_info(lbm_batch_t b, int cfg[6], void** stream) {
     if (!b) return fail(LBM_EINVAL, "null batch");
-    if (cfg) {
+    if (cfg && b->two_step) {
+        cfg[0] = lbm::kBatchFusedTX;
+        cfg[1] = lbm::kBatchFusedTY;
+        cfg[2] = 4;
+        cfg[3] = 0;
+        cfg[4] = b->ntiles2;
+        cfg[5] = b->ntiles2;
+    } else if (cfg) {
         cfg[0] = 1 << b->lbx;
         cfg[1] = (lbm::kBatchThreads >> b->lbx) * b->rows;
         cfg[2] = b->flat ? 3 : b->policy;

@@ -1,4 +1,5 @@
-// lbm_batch_bgk.cu -- persistent batch kernel for the bgk collision.
+// lbm_batch_bgk.cu -- batch kernels (one step, and two steps per launch) for the bgk collision.
+#include "lbm_batch_fused.cuh"
 #include "lbm_batch_impl.cuh"
 
 namespace lbm {
@@ -12,5 +13,9 @@ int batch_blocks_per_sm_bgk() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<LBM_BGK>, kBatchThreads, 0) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
+}
+cudaError_t launch_batch_fused_bgk(int ntiles, const BatchDomain* doms, const BatchPair* pairs, const int* tiles, int k,
+                                  const unsigned* rtab, int rstride, int kstep, int* err, cudaStream_t s) {
+    return launch_batch_fused_model<LBM_BGK>(ntiles, doms, pairs, tiles, k, rtab, rstride, kstep, err, s);
 }
 }  // namespace lbm

@@ -377,6 +377,9 @@ int after_reset(lbm_s* h) {
 
 }  // namespace
 
+cudaError_t lbm_prepare_two_step(lbm_s* h) { return ensure_fused(h); }
+const CUtensorMap& lbm_tensor_map(const lbm_s* h, const void* base) { return map_of(h, base); }
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_error.c_str(); }
@@ -552,18 +555,19 @@ static bool variant_allowed(int store, int v) {
 
 int lbm_set_variant(lbm_t h, int variant) {
     CHECK_HANDLE(h);
-    if (variant < 0 || variant > 3) return fail(LBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (variant < 0 || variant >= LBM_NUM_VARIANTS) return fail(LBM_EINVAL, "variant must be 0, 1, 2 or 3");
     const int v = variant_allowed(h->store, variant) ? variant : 0;
     if (v == 3) LBM_CUDA(ensure_fused(h), "second population array for fused steps");
     h->a.variant = v;
     return LBM_OK;
 }
 
-int lbm_tune(lbm_t h, int trial_steps, float ms[4]) {
+int lbm_tune(lbm_t h, int trial_steps, float ms[LBM_NUM_VARIANTS]) {
     CHECK_HANDLE(h);
     if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps must be >= 1");
     const int steps = trial_steps + (trial_steps & 1);  // even: the state returns to its layout
-    if (ms) ms[0] = ms[1] = ms[2] = ms[3] = 0.f;
+    if (ms)
+        for (int v = 0; v < LBM_NUM_VARIANTS; ++v) ms[v] = 0.f;
     static const int widths[4] = {128, 256, 64, 32};  // CTA shapes 128x2, 256x1, 64x4, 32x8
     const int v_prev = h->a.variant;
     // `steps` steps from step h->t as lbm_step takes them without graphs
@@ -588,7 +592,7 @@ int lbm_tune(lbm_t h, int trial_steps, float ms[4]) {
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     float best = 1e30f;
     int best_v = 0, best_w = 128;
-    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+    for (int v = 0; v < LBM_NUM_VARIANTS && e == cudaSuccess; ++v) {
         if (!variant_allowed(h->store, v)) continue;
         if (v == 3 && (ensure_fused(h) != cudaSuccess || h->check_every != 0)) {
             cudaGetLastError();  // no room for the second array: variant 3 is not a candidate

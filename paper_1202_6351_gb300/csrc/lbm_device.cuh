@@ -165,7 +165,8 @@ struct Args {
     const void* ffield;       // per-node force [2][ny][nx] (Real), or null
     double rho0;
     double scale;             // storage scale of the deviations (Store<>::scale)
-    int variant;              // 0: one node per thread; 1: two rows per thread, packed FP32x2 (FP32 arithmetic)
+    int variant;              // 0: one node per thread; 1: two rows per thread, packed FP32x2 (FP32 arithmetic);
+                              // 2: four nodes per thread (16-bit); 3: two steps per launch (lbm_fused.cuh)
     int block_x;              // CTA width of the step kernels (CTA height = 256 / block_x); 0 means 128
     // The constants the step kernels use, converted once on the host into both
     // arithmetic types (GB300's FP64 rate is far too low for per-thread

@@ -10,12 +10,14 @@
 //      a tensor copy does not do, is patched with plain loads on edge tiles);
 //   2. every node of the grown region collides in place (step t: collision of
 //      Sec. II, rounded to the storage format exactly as the one-step kernel
-//      stores it);
-//   3. every node of the tile grown by one node pulls its populations from its
-//      neighbours in shared memory, with the wall links of Sec. III-A/C, and
-//      collides (step t + 1) into a second shared buffer;
-//   4. every node of the tile pulls f(t + 2) from that buffer and writes it to
-//      the output array in the natural layout.
+//      stores it, in the AA even-step slots);
+//   3. every node of the tile grown by one node takes the AA odd step in the
+//      same buffer: it reads its populations from its neighbours' even-step
+//      slots, with the wall links of Sec. III-A/C, collides (step t + 1) and
+//      writes into the slots it read from, which no other node touches, so
+//      the step needs no second buffer;
+//   4. after the odd step the buffer holds f(t + 2) in the natural layout, and
+//      the tile goes to the output array by bulk copies, one per row and plane.
 // The per-node arithmetic and every rounding of the stored values are those of
 // two single steps (AA even step then odd step), so the result is bit for bit
 // that of lbm_step without fusion; nodes of the grown regions are computed by
@@ -26,6 +28,7 @@
 
 #include <cuda.h>
 
+#include "lbm_async.cuh"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -33,7 +36,7 @@ namespace lbm {
 // Tile geometry and launch shape per storage kind.
 template <int STORE> struct FusedTile;
 template <> struct FusedTile<LBM_F32> {
-    static constexpr int TX = 64, TY = 16, ALIGN = 4, THREADS = 512, MIN_BLOCKS = 2;
+    static constexpr int TX = 64, TY = 16, ALIGN = 4, THREADS = 256, MIN_BLOCKS = 4;
 };
 template <> struct FusedTile<LBM_F16DEV> {
     static constexpr int TX = 64, TY = 16, ALIGN = 8, THREADS = 256, MIN_BLOCKS = 4;
@@ -52,96 +55,52 @@ struct FusedGeom {
     static constexpr int RW = TX + 4, RH = TY + 4;  // region collided at step t
     static constexpr int SW = TX + 2, SH = TY + 2;  // region collided at step t + 1
     static constexpr size_t A_BYTES = size_t(9) * BH * BW * sizeof(T);
-    static constexpr size_t B_BYTES = size_t(9) * SH * SW * sizeof(T);
-    static constexpr size_t SMEM = A_BYTES + B_BYTES;
+    static constexpr size_t SMEM = A_BYTES;
     static_assert((BW * sizeof(T)) % 16 == 0 && (FT::ALIGN * sizeof(T)) == 16, "TMA box alignment");
-    static_assert(A_BYTES % 128 == 0, "second buffer alignment");
+    static_assert((TX * sizeof(T)) % 16 == 0 && TX % 32 == 0, "bulk row copies of the tile");
 };
-
-// ---------------------------------------------------------------- TMA and mbarrier (inline PTX)
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
-                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// Waits for phase `parity` of the barrier for at most `limit_ns` nanoseconds
-// (globaltimer); returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
-    unsigned long long t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > limit_ns) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
-          "r"(smem_addr(bar))
-        : "memory");
-}
 
 // Error codes the fused kernel leaves in its error word.
 enum : int { kFusedErrTimeout = 1 };
 
-// ---------------------------------------------------------------- the kernel
-// a.f is the input array (natural layout at the even step t), `out` the output
-// array (f(t + 2), natural layout); `map` describes a.f as a 3-D tensor
-// [9][ny][nx] with row pitch a.pitch.  With stochastic rounding the hashes of
-// steps t and t + 1 are a.rbase and a.rbase1, or a.rtable[a.tstep] and
-// a.rtable[a.tstep + 1] in a graph replay.
+// ---------------------------------------------------------------- one tile
+// Two steps of the tile with corner (x0, y0): `in` is the input array (natural
+// layout at the even step t), `out` the output array (f(t + 2), natural
+// layout); `map` describes `in` as a 3-D tensor [9][ny][nx] with row pitch
+// a.pitch (kernel parameter or global memory); rb0 and rb1 are the
+// stochastic-rounding hashes of steps t and t + 1.  smem holds G::SMEM bytes
+// (1024-byte aligned); bar and ok live in shared memory, and the mbarrier is
+// initialised here and used for this tile's load only.  Every thread of the
+// CTA calls this with the same arguments.
 template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
-__global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::MIN_BLOCKS)
-    fused2_kernel(const __grid_constant__ CUtensorMap map, const Args a, void* __restrict__ out,
-                  int* __restrict__ err) {
+__device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& a, const void* in, void* out,
+                                            int* err, int x0, int y0, unsigned rb0, unsigned rb1,
+                                            unsigned char* smem, unsigned long long* bar, int* ok) {
     using G = FusedGeom<STORE>;
     using S = Store<STORE>;
     using T = typename S::T;
     using R = typename S::R;
     constexpr bool TS = SR && STORE == LBM_F32;
     constexpr int NT = FusedTile<STORE>::THREADS;
-    extern __shared__ __align__(1024) unsigned char fused_smem[];
-    __shared__ __align__(8) unsigned long long bar;
-    __shared__ int ok;
-    T* A = reinterpret_cast<T*>(fused_smem);
-    T* B = reinterpret_cast<T*>(fused_smem + G::A_BYTES);
-    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    T* A = reinterpret_cast<T*>(smem);
     const int tid = threadIdx.x;
     const bool perx = !a.wall[LBM_WEST], pery = !a.wall[LBM_SOUTH];
 
     // ---- 1. the region's state at time t
     if (tid == 0) {
-        mbar_init(&bar, 1);
-        mbar_expect_tx(&bar, static_cast<unsigned>(G::A_BYTES));
-        tma_load_3d(A, &map, x0 - FusedTile<STORE>::ALIGN, y0 - 2, 0, &bar);
-        bool done = mbar_wait_bounded(&bar, 0, 1000000000ull);  // 1 s
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, static_cast<unsigned>(G::A_BYTES));
+        tma_load_3d(A, map, x0 - FusedTile<STORE>::ALIGN, y0 - 2, 0, bar);
+        bool done = mbar_wait_bounded(bar, 0, 1000000000ull);  // 1 s
         if (!done) {
             atomicOr(err, kFusedErrTimeout);
-            mbar_wait_bounded(&bar, 0, 4000000000ull);  // let the copy land before the CTA exits
+            mbar_wait_bounded(bar, 0, 4000000000ull);  // let the copy land before the CTA exits
         }
-        ok = done ? 1 : 0;
+        *ok = done ? 1 : 0;
     }
     __syncthreads();
-    if (!ok) return;
+    if (!*ok) return;
     auto Aat = [&](int q, int ry, int rxb) -> T& { return A[(q * G::BH + ry) * G::BW + rxb]; };
-    auto Bat = [&](int q, int sy, int sx) -> T& { return B[(q * G::SH + sy) * G::SW + sx]; };
     // Region coordinates lie in [-2, n + TX + 1]: one addition or subtraction of
     // n wraps them when n > TX + 2 (TY + 2 along y); smaller lattices take the modulo.
     const bool small = a.nx <= G::TX + 2 || a.ny <= G::TY + 2;
@@ -152,7 +111,7 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
 
     // periodic wrap-around of the region's halo (edge tiles only)
     if ((perx && (x0 - 2 < 0 || x0 + G::TX + 2 > a.nx)) || (pery && (y0 - 2 < 0 || y0 + G::TY + 2 > a.ny))) {
-        const T* __restrict__ f = static_cast<const T*>(a.f);
+        const T* __restrict__ f = static_cast<const T*>(in);
         for (int k = tid; k < 9 * G::RW * G::RH; k += NT) {
             const int q = k / (G::RW * G::RH), r = k % (G::RW * G::RH);
             const int ry = r / G::RW, rx = r % G::RW;
@@ -168,9 +127,8 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
     }
 
     const Coef<R> c(a);
-    const unsigned rb0 = SR ? (a.rtable ? a.rtable[a.tstep] : a.rbase) : 0u;
-    const unsigned rb1 = SR ? (a.rtable ? a.rtable[a.tstep + 1] : a.rbase1) : 0u;
-    // ---- 2. step t: collide the grown region in place (AA even step: plain stores)
+    // ---- 2. step t: collide the grown region in place (AA even step: the
+    // post-collision population q of a node goes to its own slot of plane opp(q))
     for (int k = tid; k < G::RW * G::RH; k += NT) {
         const int ry = k / G::RW, rx = k % G::RW;
         int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
@@ -191,13 +149,16 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
             if constexpr (TS) v = round_sr32(d[q], e[q], r);
             else if constexpr (SR) v = enc_sr<STORE>(d[q], r);
             else v = S::enc(d[q]);
-            Aat(q, ry, rx + G::OFF) = v;
+            Aat(opp(q), ry, rx + G::OFF) = v;
         }
     }
     __syncthreads();
 
-    // ---- 3. step t + 1 on the tile grown by one node (AA odd step: pull with
-    // the wall links, wall terms added before the rounding of the store)
+    // ---- 3. step t + 1 on the tile grown by one node, in place (AA odd step:
+    // population q arrives from slot opp(q) of the node at x - e_q, or through a
+    // wall from the node's own slot q; it leaves into slot q of the node at
+    // x + e_q, or through a wall into the node's own slot opp(q); each slot is
+    // read and written by one node only)
     for (int k = tid; k < G::SW * G::SH; k += NT) {
         const int sy = k / G::SW, sx = k % G::SW;
         int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
@@ -209,8 +170,8 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
-            if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(opp(q), ry, rxb)), q, w);
-            else d[q] = S::dec(Aat(q, ry - cy(q), rxb - cx(q)));
+            if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(q, ry, rxb)), q, w);
+            else d[q] = S::dec(Aat(opp(q), ry - cy(q), rxb - cx(q)));
         }
         R Fx, Fy;
         node_force<R, FORCE>(a, gx, gy, Fx, Fy);
@@ -234,24 +195,56 @@ __global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::M
             if constexpr (TS) o = round_sr32(v, ev, r);
             else if constexpr (SR) o = enc_sr<STORE>(v, r);
             else o = S::enc(v);
-            Bat(q, sy, sx) = o;
+            if (w >= 0) Aat(opp(q), ry, rxb) = o;
+            else Aat(q, ry + cy(q), rxb + cx(q)) = o;
         }
     }
+    fence_async_shared();  // the odd step's shared-memory writes before the bulk stores read them
     __syncthreads();
 
-    // ---- 4. f(t + 2) of the tile: pull from the second buffer, natural layout
+    // ---- 4. f(t + 2) of the tile, natural layout after the odd step: one bulk
+    // copy per row of each plane (TX elements, 16-byte aligned at both ends:
+    // x0 is a multiple of TX, the row pitch of 32 elements, the box row starts
+    // ALIGN elements left of the tile); a tile cut by the lattice's right edge
+    // is copied element by element.
     T* __restrict__ fo = static_cast<T*>(out);
-    for (int k = tid; k < G::TX * G::TY; k += NT) {
-        const int ty = k / G::TX, tx = k % G::TX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= a.nx || gy >= a.ny) continue;
-        const long long n = (long long)gy * a.pitch + gx;
+    if (x0 + G::TX <= a.nx) {
+        const int rows = min(G::TY, a.ny - y0);
+        for (int j = tid; j < 9 * rows; j += NT) {
+            const int q = j / rows, ty = j - q * rows;
+            bulk_store(fo + q * a.plane + (long long)(y0 + ty) * a.pitch + x0, &Aat(q, ty + 2, FusedTile<STORE>::ALIGN),
+                       unsigned(G::TX * sizeof(T)));
+        }
+        bulk_commit();
+        bulk_wait_read<0>();  // shared memory stays allocated until the copies have read it
+    } else {
+        for (int k = tid; k < G::TX * G::TY; k += NT) {
+            const int ty = k / G::TX, tx = k % G::TX;
+            const int gx = x0 + tx, gy = y0 + ty;
+            if (gx >= a.nx || gy >= a.ny) continue;
+            const long long n = (long long)gy * a.pitch + gx;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
-            fo[q * a.plane + n] = w >= 0 ? Bat(opp(q), ty + 1, tx + 1) : Bat(q, ty + 1 - cy(q), tx + 1 - cx(q));
+            for (int q = 0; q < 9; ++q) fo[q * a.plane + n] = Aat(q, ty + 2, tx + 2 + G::OFF);
         }
     }
+}
+
+// ---------------------------------------------------------------- the kernel
+// One CTA per tile of one lattice: a.f is the input array, `out` the output
+// array, `map` describes a.f.  With stochastic rounding the hashes of steps t
+// and t + 1 are a.rbase and a.rbase1, or a.rtable[a.tstep] and
+// a.rtable[a.tstep + 1] in a graph replay.
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+__global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::MIN_BLOCKS)
+    fused2_kernel(const __grid_constant__ CUtensorMap map, const Args a, void* __restrict__ out,
+                  int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char fused_smem[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int ok;
+    const unsigned rb0 = SR ? (a.rtable ? a.rtable[a.tstep] : a.rbase) : 0u;
+    const unsigned rb1 = SR ? (a.rtable ? a.rtable[a.tstep + 1] : a.rbase1) : 0u;
+    fused2_tile<MODEL, STORE, FORCE, WALLS, SR>(&map, a, a.f, out, err, blockIdx.x * FusedGeom<STORE>::TX,
+                                                blockIdx.y * FusedGeom<STORE>::TY, rb0, rb1, fused_smem, &bar, &ok);
 }
 
 }  // namespace lbm

@@ -43,3 +43,10 @@ struct lbm_s {
     void* tmap_ptr[2] = {nullptr, nullptr};
     int* d_err = nullptr;
 };
+
+// The second population array and the tensor maps of both arrays (variant 3),
+// made on first use; lbm_batch_* uses them for its two-step launches.
+cudaError_t lbm_prepare_two_step(lbm_s* h);
+// The tensor map of population array `base` (h->state or h->state_alt) after
+// lbm_prepare_two_step.
+const CUtensorMap& lbm_tensor_map(const lbm_s* h, const void* base);

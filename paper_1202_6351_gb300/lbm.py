@@ -21,6 +21,7 @@ WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 CASCADED, BGK, RAWMRT = 0, 1, 2
 F64, F32, BF16DEV, F16DEV = 0, 1, 2, 3
 ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
+NUM_VARIANTS = 4  # kernel variants 0..3 (lbm_set_variant)
 STORE_NAMES = {F64: "f64", F32: "f32", BF16DEV: "bf16", F16DEV: "f16"}
 MODEL_NAMES = {CASCADED: "cascaded", BGK: "bgk", RAWMRT: "rawmrt"}
 
@@ -80,6 +81,7 @@ SIGNATURES = {
     "lbm_batch_step": (_i, [_vp, _l]),
     "lbm_batch_set_graph_steps": (_i, [_vp, _i]),
     "lbm_batch_sync": (_i, [_vp]),
+    "lbm_batch_set_two_step": (_i, [_vp, _i]),
     "lbm_batch_info": (_i, [_vp, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "lbm_stats_noalloc": (_i, [_vp, C.POINTER(lbm_layout_t), _vp, _vp]),
     "lbm_last_error": (C.c_char_p, []),
@@ -269,7 +271,7 @@ class Lattice:
     def tune(self, trial_steps=20):
         """Time the kernel variants and CTA shapes, keep the fastest; returns the
         best ms per step of variants 0..3 (0.0 where the storage has no such variant)."""
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * NUM_VARIANTS)()
         _check(self.lib.lbm_tune(self.h, int(trial_steps), ms))
         return tuple(ms)
 
@@ -376,7 +378,7 @@ class Lattice:
 class Batch:
     """Many lattices advanced by one persistent launch per step (lbm_batch_*)."""
 
-    POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic", 3: "one_cta_per_tile"}
+    POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic", 3: "one_cta_per_tile", 4: "two_steps_per_launch"}
     ORDERS = {0: "largest_first", 1: "interleaved"}
 
     def __init__(self, lattices):
@@ -416,6 +418,11 @@ class Batch:
 
     def set_graph_steps(self, steps):
         _check(self.lib.lbm_batch_set_graph_steps(self.b, int(steps)))
+
+    def set_two_step(self, on=True):
+        """Two steps per launch for the whole batch (lbm_batch_set_two_step)."""
+        _check(self.lib.lbm_batch_set_two_step(self.b, 1 if on else 0))
+        return self
 
     def sync(self):
         _check(self.lib.lbm_batch_sync(self.b))

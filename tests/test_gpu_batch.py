@@ -91,6 +91,65 @@ def test_batch_is_bitwise_equal_to_single_lattice_steps(tune, rounding):
         L.close()
 
 
+# lattices of at least 4 x 4 nodes: every one admits two steps per launch
+DOMAINS_TWO_STEP = [d for d in DOMAINS if d[0] >= 4 and d[1] >= 4] + [
+    (200, 70, lbm.F32, (P, P, P, P), (0, 0, 0, 0), (0, 0), "random"),
+    (64, 16, lbm.F16DEV, (BB, BB, MW, MW), (0, 0, -0.05, 0.05), (0, 0), "random"),
+    (4, 4, lbm.BF16DEV, (P, P, P, P), (0, 0, 0, 0), (1e-5, 0), "random"),
+]
+
+
+@pytest.mark.parametrize("rounding", [False, True], ids=["nearest", "mixed_stochastic"])
+@pytest.mark.parametrize("start", [0, 1], ids=["even_start", "odd_start"])
+def test_batch_two_steps_per_launch_is_bitwise_equal_to_single_steps(start, rounding):
+    """lbm_batch_set_two_step: one CTA per 64 x 16 tile of any lattice takes two
+    steps in shared memory, the lattices' arrays trading roles at every launch;
+    an odd start or end takes one single batched step.  Every lattice ends bit for
+    bit where it ends stepped alone, across graph replays and single launches."""
+    alone = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+    batched = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+    if rounding:
+        alone = [with_rounding(L, i) for i, L in enumerate(alone)]
+        batched = [with_rounding(L, i) for i, L in enumerate(batched)]
+    for L in alone + batched:
+        L.step(start)
+    with lbm.Batch(batched) as B:
+        B.set_graph_steps(12)
+        B.set_two_step(True)
+        assert B.info()["policy"] == "two_steps_per_launch"
+        B.step(29)  # [a single step,] two replays of 6 two-step launches, single launches[, a single step]
+        B.step(4)
+        B.sync()
+    for L in alone:
+        L.step(33)
+    for i, (a, b) in enumerate(zip(alone, batched)):
+        assert a.time == b.time
+        np.testing.assert_array_equal(a.get_f(), b.get_f(), err_msg=f"domain {i}")
+    for L in alone + batched:
+        L.close()
+
+
+def test_batch_two_step_needs_4x4_lattices_and_falls_back_on_mixed_parity():
+    small = [make(DOMAINS[6], 0), make(DOMAINS[0], 1)]  # a 1 x 1 lattice
+    with lbm.Batch(small) as B:
+        with pytest.raises(lbm.LBMError):
+            B.set_two_step(True)
+    alone = [make(DOMAINS[0], 1), make(DOMAINS[3], 2)]
+    batched = [make(DOMAINS[0], 1), make(DOMAINS[3], 2)]
+    alone[0].step(1)
+    batched[0].step(1)
+    with lbm.Batch(batched) as B:
+        B.set_two_step(True)
+        B.step(6)  # parities differ: single batched steps
+        B.sync()
+    for L in alone:
+        L.step(6)
+    for a, b in zip(alone, batched):
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
+    for L in alone + batched:
+        L.close()
+
+
 def test_batch_cavity_matches_oracle():
     n, U, re = 65, 0.1, 400.0
     om = O.omega_from_nu(U * (n - 1) / re)
