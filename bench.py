@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--adjoint-n", type=int, default=512)
     p.add_argument("--adjoint-steps", type=int, default=2000)
     p.add_argument("--batch-steps", type=int, default=200)
+    p.add_argument("--batch-domains", type=int, default=96, help="first N domains of the ensemble (--part batch)")
     return p.parse_args()
 
 
@@ -640,7 +641,7 @@ def run_d3q27_extras(lbm, torch, peak, sp, n=256, steps=100):
             "state_gb": round(bpu / 2 * n ** 3 / 1e9, 2)}
 
 
-def run_batch_extras(lbm, torch, np, peak, sp, steps=200):
+def run_batch_extras(lbm, torch, np, peak, sp, steps=200, count=96):
     """Batched ensemble: 96 domains (sides log-uniform in [64, 2048], half
     lid-driven cavities at Re in [100, 5000], half Taylor-Green, FP32 / FP16
     storage), one persistent launch per step under CUDA graphs of 100 steps,
@@ -648,7 +649,7 @@ def run_batch_extras(lbm, torch, np, peak, sp, steps=200):
     cavity at Re = 5000 as the single-domain roofline point."""
     from paper_1202_6351_gb300 import workloads
 
-    doms = workloads.batch_domains()
+    doms = workloads.batch_domains()[:count]  # fewer domains only for profiling captures
     Ls, nodes, nbytes = [], 0, 0
     for i, d in enumerate(doms):
         n = d["side"]
@@ -904,7 +905,7 @@ def run_part(args):
     if args.part == "adjoint":
         out = run_adjoint_extras(lbm, torch, np, sp, n=args.adjoint_n, steps=args.adjoint_steps, peak=peak)
     elif args.part == "batch":
-        out = run_batch_extras(lbm, torch, np, peak, sp, steps=args.batch_steps)
+        out = run_batch_extras(lbm, torch, np, peak, sp, steps=args.batch_steps, count=args.batch_domains)
     else:
         from paper_1202_6351_gb300 import workloads
 

@@ -30,6 +30,7 @@
 
 #include "lbm_async.cuh"
 #include "lbm_device.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -62,6 +63,117 @@ struct FusedGeom {
 
 // Error codes the fused kernel leaves in its error word.
 enum : int { kFusedErrTimeout = 1 };
+
+// ---------------------------------------------------------------- packed stages
+// Stages 2 and 3 of a tile with two nodes per thread (the k-th and the
+// (k + half)-th node of the region) collided together in packed FP32x2
+// arithmetic; loads, conversions, wall links and stores stay per node.  A node
+// beyond a wall (or the missing partner of an odd region) is collided on
+// whatever its slots hold and not stored.
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+__device__ __forceinline__ void fused2_pack_stages(const Args& a, typename Store<STORE>::T* A, int x0, int y0,
+                                                   unsigned rb0, unsigned rb1) {
+    using G = FusedGeom<STORE>;
+    using S = Store<STORE>;
+    using T = typename S::T;
+    constexpr int NT = FusedTile<STORE>::THREADS;
+    const int tid = threadIdx.x;
+    const bool perx = !a.wall[LBM_WEST], pery = !a.wall[LBM_SOUTH];
+    auto Aat = [&](int q, int ry, int rxb) -> T& { return A[(q * G::BH + ry) * G::BW + rxb]; };
+    const bool small = a.nx <= G::TX + 2 || a.ny <= G::TY + 2;
+    auto wrap = [small](int v, int n) {
+        if (small) return ((v % n) + n) % n;
+        return v < 0 ? v + n : (v >= n ? v - n : v);
+    };
+    const Coef<F2> c2 = pair_coef(a);
+    auto enc = [&](float v, unsigned rn, int q) -> T {
+        if constexpr (SR) return enc_sr<STORE>(v, rn + static_cast<unsigned>(q) * kRoundStride);
+        else return S::enc(v);
+    };
+
+    // ---- 2. step t on the grown region (AA even step, in place)
+    constexpr int N2 = G::RW * G::RH, H2 = (N2 + 1) / 2;
+    for (int k = tid; k < H2; k += NT) {
+        int ry[2], rx[2], gx[2], gy[2];
+        bool ok[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int kk = k + j * H2 < N2 ? k + j * H2 : k;
+            ry[j] = kk / G::RW;
+            rx[j] = kk % G::RW;
+            gx[j] = x0 - 2 + rx[j];
+            gy[j] = y0 - 2 + ry[j];
+            ok[j] = k + j * H2 < N2 && !((!perx && (gx[j] < 0 || gx[j] >= a.nx)) || (!pery && (gy[j] < 0 || gy[j] >= a.ny)));
+            gx[j] = wrap(gx[j], a.nx);
+            gy[j] = wrap(gy[j], a.ny);
+        }
+        F2 d[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            d[q] = F2(make_float2(S::dec(Aat(q, ry[0], rx[0] + G::OFF)), S::dec(Aat(q, ry[1], rx[1] + G::OFF))));
+        float fx[2], fy[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) node_force<float, FORCE>(a, gx[j], gy[j], fx[j], fy[j]);
+        collide<MODEL, F2, (FORCE != 0)>(d, F2(make_float2(fx[0], fx[1])), F2(make_float2(fy[0], fy[1])), c2);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (!ok[j]) continue;
+            const unsigned rn = SR ? round_node(a, rb0, gx[j], gy[j]) : 0u;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Aat(opp(q), ry[j], rx[j] + G::OFF) = enc(j ? d[q].v.y : d[q].v.x, rn, q);
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. step t + 1 on the tile grown by one node (AA odd step, in place)
+    constexpr int N3 = G::SW * G::SH, H3 = (N3 + 1) / 2;
+    for (int k = tid; k < H3; k += NT) {
+        int ry[2], rxb[2], gx[2], gy[2];
+        bool ok[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int kk = k + j * H3 < N3 ? k + j * H3 : k;
+            const int sy = kk / G::SW, sx = kk % G::SW;
+            gx[j] = x0 - 1 + sx;
+            gy[j] = y0 - 1 + sy;
+            ok[j] = k + j * H3 < N3 && !((!perx && (gx[j] < 0 || gx[j] >= a.nx)) || (!pery && (gy[j] < 0 || gy[j] >= a.ny)));
+            gx[j] = wrap(gx[j], a.nx);
+            gy[j] = wrap(gy[j], a.ny);
+            ry[j] = sy + 1;
+            rxb[j] = sx + 1 + G::OFF;
+        }
+        F2 d[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            float v[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int w = WALLS ? incoming_wall(a, q, gx[j], gy[j]) : -1;
+                if (w >= 0) v[j] = add_wall_term<float>(a, S::dec(Aat(q, ry[j], rxb[j])), q, w);
+                else v[j] = S::dec(Aat(opp(q), ry[j] - cy(q), rxb[j] - cx(q)));
+            }
+            d[q] = F2(make_float2(v[0], v[1]));
+        }
+        float fx[2], fy[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) node_force<float, FORCE>(a, gx[j], gy[j], fx[j], fy[j]);
+        collide<MODEL, F2, (FORCE != 0)>(d, F2(make_float2(fx[0], fx[1])), F2(make_float2(fy[0], fy[1])), c2);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (!ok[j]) continue;
+            const unsigned rn = SR ? round_node(a, rb1, gx[j], gy[j]) : 0u;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int w = WALLS ? incoming_wall(a, opp(q), gx[j], gy[j]) : -1;
+                float v = j ? d[q].v.y : d[q].v.x;
+                if (w >= 0) v = add_wall_term<float>(a, v, opp(q), w);
+                const T o = enc(v, rn, q);
+                if (w >= 0) Aat(opp(q), ry[j], rxb[j]) = o;
+                else Aat(q, ry[j] + cy(q), rxb[j] + cx(q)) = o;
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------- one tile
 // Two steps of the tile with corner (x0, y0): `in` is the input array (natural
@@ -127,6 +239,18 @@ __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& 
     }
 
     const Coef<R> c(a);
+    // Two nodes per thread in packed FP32x2 arithmetic where the packed
+    // collision rounds every value exactly as the scalar one (the cascaded
+    // collision without forcing, FP32 storage, round to nearest) and the
+    // registers suffice (no walls): 4-5 % faster there.  With forcing and in
+    // the siblings the compiler contracts some single-use products of the
+    // scalar code into the next addition across statements, which the packed
+    // code rounds separately (a unit in the last place apart); with walls the
+    // packed stages spill; 16-bit storage runs slower packed.
+    constexpr bool PACK = MODEL == LBM_CASCADED && FORCE == 0 && STORE == LBM_F32 && !SR && !WALLS;
+    if constexpr (PACK) {
+        fused2_pack_stages<MODEL, STORE, FORCE, WALLS, SR>(a, A, x0, y0, rb0, rb1);
+    } else {
     // ---- 2. step t: collide the grown region in place (AA even step: the
     // post-collision population q of a node goes to its own slot of plane opp(q))
     for (int k = tid; k < G::RW * G::RH; k += NT) {
@@ -199,6 +323,7 @@ __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& 
             else Aat(q, ry + cy(q), rxb + cx(q)) = o;
         }
     }
+    }  // one node per thread
     fence_async_shared();  // the odd step's shared-memory writes before the bulk stores read them
     __syncthreads();
 

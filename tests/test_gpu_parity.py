@@ -594,6 +594,10 @@ FUSED_CASES = [  # (nx, ny, edges, force, force field, store, rounding)
     (4, 4, "cavity", (0.0, 0.0), False, lbm.F16DEV, False),
     (90, 40, "allmoving", (1e-5, -2e-5), False, lbm.F32, False),
     (77, 50, "ychannel", (0.0, 3e-5), False, lbm.BF16DEV, True),
+    # periodic, unforced FP32: the cascaded collision runs in packed FP32x2 pairs here
+    (130, 33, "periodic", (0.0, 0.0), False, lbm.F32, False),
+    (64, 16, "periodic", (0.0, 0.0), False, lbm.F32, False),
+    (4, 4, "periodic", (0.0, 0.0), False, lbm.F32, False),
 ]
 
 
@@ -607,7 +611,8 @@ def test_fused_two_step_variant_is_bitwise_equal_to_single_steps(model, case):
     rounding of the stored values are those of two single steps, so the states
     agree bit for bit: across ragged tiles, lattice edges with periodic wrap,
     walls and moving walls, forces and force fields, stochastic rounding, an odd
-    start, and CUDA-graph replays."""
+    start, and CUDA-graph replays; also where the kernel collides node pairs in
+    packed FP32x2 arithmetic (periodic, unforced, FP32, cascaded)."""
     nx, ny, edges, force, field, store, sr = case
     e, wu = EDGES[edges]
     rho, u = workloads.random_fields(71, nx, ny, u_amp=0.03, rho_amp=0.01)
