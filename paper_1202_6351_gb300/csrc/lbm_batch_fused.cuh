@@ -33,6 +33,10 @@ static_assert(FusedTile<LBM_F32>::THREADS == FusedTile<LBM_F16DEV>::THREADS &&
                   FusedGeom<LBM_F32>::TX == FusedGeom<LBM_F16DEV>::TX && FusedGeom<LBM_F32>::TY == FusedGeom<LBM_F16DEV>::TY,
               "one tile shape and CTA size for every storage kind");
 constexpr int kBatchFusedThreads = FusedTile<LBM_F32>::THREADS;
+// The packed FP32x2 stages of the two-step tile (lbm_fused.cuh) in the batch
+// kernel, which carries every storage, edge, force and rounding path in one
+// kernel.
+constexpr bool kBatchPacked = false;
 constexpr int kBatchFusedTX = FusedGeom<LBM_F32>::TX, kBatchFusedTY = FusedGeom<LBM_F32>::TY;
 
 template <int MODEL, int STORE, int FORCE, bool WALLS>
@@ -40,11 +44,11 @@ __device__ __forceinline__ void batch_fused_sr(const BatchPair& P, const Args& a
                                                unsigned rb0, unsigned rb1, unsigned char* smem,
                                                unsigned long long* bar, int* ok) {
     if (a.rseed)
-        fused2_tile<MODEL, STORE, FORCE, WALLS, true>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0, y0, rb0, rb1,
-                                                      smem, bar, ok);
+        fused2_tile<MODEL, STORE, FORCE, WALLS, true, kBatchPacked>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0,
+                                                                    y0, rb0, rb1, smem, bar, ok);
     else
-        fused2_tile<MODEL, STORE, FORCE, WALLS, false>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0, y0, 0u, 0u,
-                                                       smem, bar, ok);
+        fused2_tile<MODEL, STORE, FORCE, WALLS, false, kBatchPacked>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0,
+                                                                     y0, 0u, 0u, smem, bar, ok);
 }
 
 template <int MODEL, int STORE>

@@ -58,7 +58,7 @@ struct FusedGeom {
     static constexpr size_t A_BYTES = size_t(9) * BH * BW * sizeof(T);
     static constexpr size_t SMEM = A_BYTES;
     static_assert((BW * sizeof(T)) % 16 == 0 && (FT::ALIGN * sizeof(T)) == 16, "TMA box alignment");
-    static_assert((TX * sizeof(T)) % 16 == 0 && TX % 32 == 0, "bulk row copies of the tile");
+    static_assert((TX * sizeof(T)) % 16 == 0, "bulk row copies of the tile start and end on 16-byte boundaries");
 };
 
 // Error codes the fused kernel leaves in its error word.
@@ -183,8 +183,9 @@ __device__ __forceinline__ void fused2_pack_stages(const Args& a, typename Store
 // stochastic-rounding hashes of steps t and t + 1.  smem holds G::SMEM bytes
 // (1024-byte aligned); bar and ok live in shared memory, and the mbarrier is
 // initialised here and used for this tile's load only.  Every thread of the
-// CTA calls this with the same arguments.
-template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+// CTA calls this with the same arguments.  PACKED false keeps one node per
+// thread everywhere.
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR, bool PACKED = true>
 __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& a, const void* in, void* out,
                                             int* err, int x0, int y0, unsigned rb0, unsigned rb1,
                                             unsigned char* smem, unsigned long long* bar, int* ok) {
@@ -247,7 +248,7 @@ __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& 
     // scalar code into the next addition across statements, which the packed
     // code rounds separately (a unit in the last place apart); with walls the
     // packed stages spill; 16-bit storage runs slower packed.
-    constexpr bool PACK = MODEL == LBM_CASCADED && FORCE == 0 && STORE == LBM_F32 && !SR && !WALLS;
+    constexpr bool PACK = PACKED && MODEL == LBM_CASCADED && FORCE == 0 && STORE == LBM_F32 && !SR && !WALLS;
     if constexpr (PACK) {
         fused2_pack_stages<MODEL, STORE, FORCE, WALLS, SR>(a, A, x0, y0, rb0, rb1);
     } else {
