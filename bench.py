@@ -623,24 +623,31 @@ def run_d3q27_extras(lbm, torch, peak, sp, n=256, steps=100):
     """The D3Q27 central-moment lattice (the method carried to 3-D): the 3-D
     Taylor-Green vortex on n^3 periodic nodes in FP32 storage, one launch per
     step; MLUPS and the fraction of the copy bandwidth at 216 B per update
-    (27 loads and 27 stores of 4 bytes)."""
+    (27 loads and 27 stores of 4 bytes); the same in FP16 storage (108 B)."""
     from paper_1202_6351_gb300 import workloads
 
     rho, u = workloads.taylor_green_3d_init(n, 0.04 * 64 / n)
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with lbm.Lattice3(n, n, n, (1.0, OMEGA, 1.0, 1.0, 1.0, 1.0), store=lbm.F32, stream=sp) as L:
-        L.init(rho, u).step(4)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        L.step(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-    bpu = lbm.load_library().lbm3_bytes_per_update(lbm.F32)
-    return {"workload": f"taylor_green_3d_{n}^3_d3q27_f32", "steps": steps, "mlups": round(n ** 3 * steps / t / 1e6, 1),
-            "frac": round(bpu * n ** 3 * steps / t / 1e9 / peak, 4), "bytes_per_update": bpu,
-            "state_gb": round(bpu / 2 * n ** 3 / 1e9, 2)}
+    out = {}
+    for name, st in (("f32", lbm.F32), ("f16", lbm.F16DEV)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with lbm.Lattice3(n, n, n, (1.0, OMEGA, 1.0, 1.0, 1.0, 1.0), store=st, stream=sp) as L:
+            L.init(rho, u).step(4)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            L.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+        bpu = lbm.load_library().lbm3_bytes_per_update(st)
+        entry = {"workload": f"taylor_green_3d_{n}^3_d3q27_{name}", "steps": steps,
+                 "mlups": round(n ** 3 * steps / t / 1e6, 1), "frac": round(bpu * n ** 3 * steps / t / 1e9 / peak, 4),
+                 "bytes_per_update": bpu, "state_gb": round(bpu / 2 * n ** 3 / 1e9, 2)}
+        if name == "f32":
+            out.update(entry)
+        else:
+            out["f16"] = entry
+    return out
 
 
 def run_batch_extras(lbm, torch, np, peak, sp, steps=200, count=96):

@@ -39,7 +39,9 @@ typedef struct lbm3_s* lbm3_t;
 /* Create a periodic nx x ny x nz D3Q27 lattice on the current device, at rest
  * (f = w rho0).  omegas = (omega_bulk, omega_shear, omega_3, omega_4, omega_5,
  * omega_6), each in (0, 2); force = uniform (F_x, F_y, F_z) or NULL; store =
- * LBM_F64 or LBM_F32.  Allocates 27 * pitch * ny * nz elements (pitch = nx
+ * LBM_F64, LBM_F32, LBM_BF16DEV or LBM_F16DEV (deviations f - w rho0 as in
+ * include/lbm.h; FP16 holds 4096 times the deviation; the 16-bit kinds round
+ * to nearest even).  Allocates 27 * pitch * ny * nz elements (pitch = nx
  * rounded up to 32).  Errors: LBM_EINVAL (sizes < 1, nz > 65535, padded plane
  * >= 2^31 elements, omega outside (0, 2), other storage kinds, rho0 <= 0,
  * non-finite force, out == NULL), LBM_ENOMEM, LBM_ECUDA. */
@@ -68,7 +70,7 @@ long lbm3_time(lbm3_t h);                   /* -1 for NULL */
 /* dims = (nx, ny, nz, pitch, store); bytes and state of the population array */
 int lbm3_info(lbm3_t h, long dims[5], size_t* bytes, void** state);
 /* Algorithmic bytes of one lattice update: 27 loads and 27 stores (432 FP64,
- * 216 FP32; 0 for other kinds). */
+ * 216 FP32, 108 BF16/FP16; 0 for other kinds). */
 size_t lbm3_bytes_per_update(int store);
 
 #ifdef __cplusplus

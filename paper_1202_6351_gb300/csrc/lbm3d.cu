@@ -7,6 +7,7 @@
 // deviations; FP32 arithmetic for FP32 storage.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "lbm3d.h"
 #include "lbm3d_device.cuh"
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kBX * kBY) init3_kernel(const Args3 a, const d
     const long long p = ((long long)z * a.ny + y) * a.nx + x, n = (long long)a.nx * a.ny * a.nz;
     const R* k = lbm3::kconst3<R>(a);
     const R rho0 = k[lbm3::K3_RHO0];
-    const R drho = rho ? R(rho[p] - a.kd[lbm3::K3_RHO0]) : R(0);
+    const R drho = rho ? R((rho[p] - a.kd[lbm3::K3_RHO0]) * a.scale) : R(0);  // stored units
     const R ux = u ? R(u[p]) : R(0), uy = u ? R(u[n + p]) : R(0), uz = u ? R(u[2 * n + p]) : R(0);
     R d[27];
     lbm3::equilibrium3<R>(d, rho0, drho, ux, uy, uz, k[lbm3::K3_FX], k[lbm3::K3_FY], k[lbm3::K3_FZ]);
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kBX * kBY) get3_kernel(const Args3 a, bool odd
     else lbm3::load3<STORE, false>(a, x, y, z, d);
     const long long p = ((long long)z * a.ny + y) * a.nx + x, n = (long long)a.nx * a.ny * a.nz;
 #pragma unroll
-    for (int q = 0; q < 27; ++q) out[q * n + p] = double(d[q]) + lbm3::wgt<double>(q) * a.kd[lbm3::K3_RHO0];
+    for (int q = 0; q < 27; ++q) out[q * n + p] = double(d[q]) / a.scale + lbm3::wgt<double>(q) * a.kd[lbm3::K3_RHO0];
 }
 
 template <int STORE>
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kBX * kBY) set3_kernel(const Args3 a, const do
     const long long o = lbm3::node_off<T>(a, x, y, z);
 #pragma unroll
     for (int q = 0; q < 27; ++q)
-        f[q * a.plane + o] = S::enc(typename S::R(in[q * n + p] - lbm3::wgt<double>(q) * a.kd[lbm3::K3_RHO0]));
+        f[q * a.plane + o] = S::enc(typename S::R((in[q * n + p] - lbm3::wgt<double>(q) * a.kd[lbm3::K3_RHO0]) * a.scale));
 }
 
 // rho, u (Eq. 26-27 in 3-D, with F/2) into FP64 device arrays (either may be null).
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(kBX * kBY) macros3_kernel(const Args3 a, bool 
         j[1] += lbm3::ey(q) * v;
         j[2] += lbm3::ez(q) * v;
     }
+    drho /= a.scale;
+    for (int k = 0; k < 3; ++k) j[k] /= a.scale;
     const double r = a.kd[lbm3::K3_RHO0] + drho;
     const long long p = ((long long)z * a.ny + y) * a.nx + x, n = (long long)a.nx * a.ny * a.nz;
     if (rho) rho[p] = r;
@@ -155,12 +158,22 @@ struct lbm3_s {
 
 namespace {
 
-size_t es3(int store) { return store == LBM_F64 ? 8 : 4; }
+size_t es3(int store) { return store == LBM_F64 ? 8 : (store == LBM_F32 ? 4 : 2); }
+
+// fn(std::integral_constant<int, STORE>) for the lattice's storage kind.
+template <typename Fn>
+void with_store(int store, Fn&& fn) {
+    switch (store) {
+        case LBM_F64: fn(std::integral_constant<int, LBM_F64>()); break;
+        case LBM_F32: fn(std::integral_constant<int, LBM_F32>()); break;
+        case LBM_BF16DEV: fn(std::integral_constant<int, LBM_BF16DEV>()); break;
+        default: fn(std::integral_constant<int, LBM_F16DEV>()); break;
+    }
+}
 
 cudaError_t run_init(lbm3_s* h, const double* rho, const double* u) {
     const dim3 g = grid_of(h->a), b(kBX, kBY);
-    if (h->store == LBM_F64) init3_kernel<LBM_F64><<<g, b, 0, h->stream>>>(h->a, rho, u);
-    else init3_kernel<LBM_F32><<<g, b, 0, h->stream>>>(h->a, rho, u);
+    with_store(h->store, [&](auto st) { init3_kernel<decltype(st)::value><<<g, b, 0, h->stream>>>(h->a, rho, u); });
     return cudaGetLastError();
 }
 
@@ -204,7 +217,8 @@ int lbm3_create(int nx, int ny, int nz, const double omegas[6], const double for
     if (!omegas) return fail(LBM_EINVAL, "lbm3_create: omegas is NULL");
     for (int k = 0; k < 6; ++k)
         if (!(omegas[k] > 0.0 && omegas[k] < 2.0)) return fail(LBM_EINVAL, "lbm3_create: every omega must lie in (0, 2)");
-    if (store != LBM_F64 && store != LBM_F32) return fail(LBM_EINVAL, "lbm3_create: storage must be LBM_F64 or LBM_F32");
+    if (store != LBM_F64 && store != LBM_F32 && store != LBM_BF16DEV && store != LBM_F16DEV)
+        return fail(LBM_EINVAL, "lbm3_create: storage must be LBM_F64, LBM_F32, LBM_BF16DEV or LBM_F16DEV");
     if (!(rho0 > 0.0 && std::isfinite(rho0))) return fail(LBM_EINVAL, "lbm3_create: rho0 must be positive and finite");
     if (force && !(std::isfinite(force[0]) && std::isfinite(force[1]) && std::isfinite(force[2])))
         return fail(LBM_EINVAL, "lbm3_create: force must be finite");
@@ -223,7 +237,8 @@ int lbm3_create(int nx, int ny, int nz, const double omegas[6], const double for
     for (int k = 0; k < 6; ++k) a.kd[k] = omegas[k];
     a.kd[lbm3::K3_RHO0] = rho0;
     for (int k = 0; k < 3; ++k) a.kd[lbm3::K3_FX + k] = force ? force[k] : 0.0;
-    for (int k = 0; k < 10; ++k) a.kf[k] = float(a.kd[k]);
+    a.scale = lbm::store_scale(store);
+    for (int k = 0; k < 10; ++k) a.kf[k] = float(k >= lbm3::K3_RHO0 ? a.kd[k] * a.scale : a.kd[k]);
     h->forced = force && (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0);
     h->state_bytes = 27 * size_t(a.plane) * es3(store);
     cudaError_t e = cudaMalloc(&h->state, h->state_bytes);
@@ -283,8 +298,8 @@ int lbm3_step(lbm3_t h, long n) {
     if (n < 0) return fail(LBM_EINVAL, "lbm3_step: n must be >= 0");
     for (long s = 0; s < n; ++s) {
         const bool odd = (h->t & 1) != 0;
-        const cudaError_t e = h->store == LBM_F64 ? launch_step3<LBM_F64>(h->a, odd, h->forced, h->stream)
-                                                  : launch_step3<LBM_F32>(h->a, odd, h->forced, h->stream);
+        cudaError_t e = cudaSuccess;
+        with_store(h->store, [&](auto st) { e = launch_step3<decltype(st)::value>(h->a, odd, h->forced, h->stream); });
         if (e != cudaSuccess) return cuda_fail(e, "lbm3_step launch");
         ++h->t;
     }
@@ -301,8 +316,7 @@ int lbm3_macros(lbm3_t h, double* rho, double* u) {
     double* du = drho + n;
     const dim3 g = grid_of(h->a), b(kBX, kBY);
     const bool odd = (h->t & 1) != 0;
-    if (h->store == LBM_F64) macros3_kernel<LBM_F64><<<g, b, 0, h->stream>>>(h->a, odd, drho, du);
-    else macros3_kernel<LBM_F32><<<g, b, 0, h->stream>>>(h->a, odd, drho, du);
+    with_store(h->store, [&](auto st) { macros3_kernel<decltype(st)::value><<<g, b, 0, h->stream>>>(h->a, odd, drho, du); });
     L3_CUDA(cudaGetLastError(), "lbm3_macros kernel");
     if (rho) L3_CUDA(cudaMemcpyAsync(rho, drho, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "rho copy");
     if (u) L3_CUDA(cudaMemcpyAsync(u, du, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "u copy");
@@ -318,8 +332,9 @@ int lbm3_get_f(lbm3_t h, double* f) {
     L3_CUDA(buf.alloc(n * sizeof(double)), "lbm3_get_f staging");
     const dim3 g = grid_of(h->a), b(kBX, kBY);
     const bool odd = (h->t & 1) != 0;
-    if (h->store == LBM_F64) get3_kernel<LBM_F64><<<g, b, 0, h->stream>>>(h->a, odd, static_cast<double*>(buf.p));
-    else get3_kernel<LBM_F32><<<g, b, 0, h->stream>>>(h->a, odd, static_cast<double*>(buf.p));
+    with_store(h->store, [&](auto st) {
+        get3_kernel<decltype(st)::value><<<g, b, 0, h->stream>>>(h->a, odd, static_cast<double*>(buf.p));
+    });
     L3_CUDA(cudaGetLastError(), "lbm3_get_f kernel");
     L3_CUDA(cudaMemcpyAsync(f, buf.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "f copy");
     L3_CUDA(cudaStreamSynchronize(h->stream), "lbm3_get_f sync");
@@ -334,8 +349,9 @@ int lbm3_set_f(lbm3_t h, const double* f) {
     L3_CUDA(buf.alloc(n * sizeof(double)), "lbm3_set_f staging");
     L3_CUDA(cudaMemcpyAsync(buf.p, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "f copy");
     const dim3 g = grid_of(h->a), b(kBX, kBY);
-    if (h->store == LBM_F64) set3_kernel<LBM_F64><<<g, b, 0, h->stream>>>(h->a, static_cast<const double*>(buf.p));
-    else set3_kernel<LBM_F32><<<g, b, 0, h->stream>>>(h->a, static_cast<const double*>(buf.p));
+    with_store(h->store, [&](auto st) {
+        set3_kernel<decltype(st)::value><<<g, b, 0, h->stream>>>(h->a, static_cast<const double*>(buf.p));
+    });
     L3_CUDA(cudaGetLastError(), "lbm3_set_f kernel");
     L3_CUDA(cudaStreamSynchronize(h->stream), "lbm3_set_f sync");
     h->t = 0;
@@ -358,6 +374,8 @@ int lbm3_info(lbm3_t h, long dims[5], size_t* bytes, void** state) {
     return LBM_OK;
 }
 
-size_t lbm3_bytes_per_update(int store) { return store == LBM_F64 ? 54 * 8 : (store == LBM_F32 ? 54 * 4 : 0); }
+size_t lbm3_bytes_per_update(int store) {
+    return (store == LBM_F64 || store == LBM_F32 || store == LBM_BF16DEV || store == LBM_F16DEV) ? 54 * es3(store) : 0;
+}
 
 }  // extern "C"

@@ -45,8 +45,9 @@ struct Args3 {
     void* f;             // populations [27][nz][ny][pitch] of the stored type (deviations)
     long long plane;     // pitch * ny * nz
     int nx, ny, nz, pitch;
-    double kd[10];       // omega_bulk, omega_shear, omega_3..omega_6, rho0, F_x, F_y, F_z
-    float kf[10];
+    double kd[10];       // omega_bulk, omega_shear, omega_3..omega_6, rho0, F_x, F_y, F_z (physical units)
+    float kf[10];        // the same in FP32, rho0 and F times `scale` (the step works in stored units)
+    double scale;        // storage scale of the deviations (Store<>::scale: 4096 for FP16, else 1)
 };
 enum : int { K3_OB = 0, K3_OS = 1, K3_O3 = 2, K3_RHO0 = 6, K3_FX = 7, K3_FY = 8, K3_FZ = 9 };
 

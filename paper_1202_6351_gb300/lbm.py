@@ -438,8 +438,8 @@ class Batch:
 class Lattice3:
     """A periodic D3Q27 central-moment lattice (lbm3_* of include/lbm3d.h).
     omegas = (omega_bulk, omega_shear, omega_3, omega_4, omega_5, omega_6);
-    host arrays are numpy float64: rho [nz, ny, nx], u [3, nz, ny, nx],
-    f [27, nz, ny, nx]."""
+    store = F64, F32, BF16DEV or F16DEV; host arrays are numpy float64:
+    rho [nz, ny, nx], u [3, nz, ny, nx], f [27, nz, ny, nx]."""
 
     def __init__(self, nx, ny, nz, omegas, force=(0.0, 0.0, 0.0), store=F32, rho0=1.0, stream=None):
         self.lib = load_library()

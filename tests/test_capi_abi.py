@@ -158,7 +158,7 @@ def test_null_handles_of_the_tuning_rounding_batch_and_adjoint_calls():
 
 BAD_CREATE3 = [
     dict(nx=0), dict(nz=0), dict(nz=70000), dict(nx=2048, ny=2048, nz=1024),
-    dict(omegas=(1.0, 2.0, 1.0, 1.0, 1.0, 1.0)), dict(store=lbm.F16DEV), dict(rho0=-1.0),
+    dict(omegas=(1.0, 2.0, 1.0, 1.0, 1.0, 1.0)), dict(store=7), dict(rho0=-1.0),
     dict(force=(float("nan"), 0.0, 0.0)),
 ]
 
@@ -182,4 +182,5 @@ def test_d3q27_null_handles():
     assert lib.lbm3_macros(None, None, None) == lbm.LBM_EINVAL
     assert lib.lbm3_time(None) == -1
     assert lib.lbm3_bytes_per_update(lbm.F32) == 216 and lib.lbm3_bytes_per_update(lbm.F64) == 432
-    assert lib.lbm3_bytes_per_update(lbm.F16DEV) == 0
+    assert lib.lbm3_bytes_per_update(lbm.F16DEV) == 108 and lib.lbm3_bytes_per_update(lbm.BF16DEV) == 108
+    assert lib.lbm3_bytes_per_update(7) == 0
