@@ -464,8 +464,17 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with pinned host buffers (every rank, right
     # after the timed region so that it runs under the same conditions each time)
+    esampler = ClockSampler(uuid) if rank == 0 else None
+    if esampler:
+        esampler.wait_first()
+    e0w = time.time()
     e2e = run_e2e(args, lbm, torch, np, n, rho_h, u_h, sp, nodes, barrier,
                   lambda v: max_over_ranks(v, dist, "cuda"), world)
+    e1w = time.time()
+    if esampler:
+        time.sleep(0.3)
+        esampler.stop()
+        e2e["clocks"] = esampler.summary(e0w, e1w)  # SM clocks while the end-to-end sequences ran
 
     extras = {}
     if rank == 0 and not args.no_extras:
