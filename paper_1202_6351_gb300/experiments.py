@@ -335,8 +335,9 @@ def cavity_matrix(n, res=(1000.0, 3200.0, 5000.0), models=(lbm.CASCADED, lbm.BGK
     (nu = U (n - 1) / Re, other rates 1, from rest; Sec. IV-C, V) for each
     collision model, each in FP32 storage and, if `f16`, in FP16 storage with
     round to nearest and with stochastic rounding.  All lattices of one model
-    advance together in one batched launch per step (lbm.Batch); the batches of
-    the models run on their own streams at the same time.
+    advance together in one batched launch per two steps (lbm.Batch with two
+    steps per launch); the batches of the models run on their own streams at
+    the same time.
 
     A case (model, Re) runs until its FP32 lattice is steady (max |u(t) -
     u(t - check)| < tol) or blows up (a non-finite velocity or |u| > 1), or
@@ -376,7 +377,10 @@ def cavity_matrix(n, res=(1000.0, 3200.0, 5000.0), models=(lbm.CASCADED, lbm.BGK
         for model in models:
             ls = [L for (m, _), c in cases.items() if m == model and c["result"] is None for L in c["lattices"].values()]
             if ls:
-                out.append(lbm.Batch(ls))
+                B = lbm.Batch(ls)
+                if n >= 4:
+                    B.set_two_step(True)  # two steps per launch; bit for bit the same states
+                out.append(B)
         return out
 
     live = batches()
