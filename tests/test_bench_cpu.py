@@ -83,3 +83,12 @@ def test_launch_count_of_fused_and_single_steps():
     assert bench.launch_count(0, 20, True) == 10
     assert bench.launch_count(5, 20, True) == 11  # one single step, nine pairs, one single step
     assert bench.launch_count(1, 1, True) == 1
+
+
+def test_profile_summary_was_taken_on_the_current_step_kernels():
+    """profiles/step_cascaded_tg4096.md records the digest of the step-kernel
+    sources its ncu counters were taken on; bench.py reports roofline.traffic
+    only while that digest matches.  The committed summary must describe the
+    committed kernels (every figure bench.py reads is there)."""
+    for key in ("f32", "f16", "f32_two_step"):
+        assert bench.profiled_traffic(key) is not None, key
