@@ -129,6 +129,30 @@ def test_batch_two_steps_per_launch_is_bitwise_equal_to_single_steps(start, roun
         L.close()
 
 
+def test_batch_tuner_with_the_two_step_candidate_leaves_states_unchanged():
+    """The batch tuner also times two steps per launch when every lattice admits
+    it and all are at the same even step; its trial launches swap each
+    lattice's two arrays an even number of times and the states are restored,
+    so tuning changes nothing, and the steps after it match single steps bit
+    for bit whichever configuration it keeps."""
+    alone = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+    batched = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+    with lbm.Batch(batched) as B:
+        before = [L.get_f() for L in batched]
+        B.tune(4)
+        for L, f in zip(batched, before):
+            np.testing.assert_array_equal(L.get_f(), f)
+        assert B.info()["policy"] in ("round_robin", "chunked", "dynamic", "one_cta_per_tile", "two_steps_per_launch")
+        B.step(22)
+        B.sync()
+    for L in alone:
+        L.step(22)
+    for i, (a, b) in enumerate(zip(alone, batched)):
+        np.testing.assert_array_equal(a.get_f(), b.get_f(), err_msg=f"domain {i}")
+    for L in alone + batched:
+        L.close()
+
+
 def test_batch_two_step_needs_4x4_lattices_and_falls_back_on_mixed_parity():
     small = [make(DOMAINS[6], 0), make(DOMAINS[0], 1)]  # a 1 x 1 lattice
     with lbm.Batch(small) as B:
