@@ -252,20 +252,28 @@ cudaError_t prepare_two_step(lbm_batch_s* b) {
             for (int i = 0; i < tx; ++i) t.insert(t.end(), {d, i, j});
     }
     lbm::BatchPair* hp = nullptr;
+    lbm::BatchPair* dp = nullptr;
+    int* dt = nullptr;
+    int* de = nullptr;
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hp, b->doms.size() * sizeof(lbm::BatchPair));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_pairs, b->doms.size() * sizeof(lbm::BatchPair));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles2, t.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_tiles2, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dp, b->doms.size() * sizeof(lbm::BatchPair));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dt, t.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&de, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(de, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // t is a local vector
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess) {  // nothing kept: a later call starts over
         if (hp) cudaFreeHost(hp);
+        if (dp) cudaFree(dp);
+        if (dt) cudaFree(dt);
+        if (de) cudaFree(de);
         return e;
     }
     b->ntiles2 = int(t.size() / 3);
     b->h_pairs = hp;
+    b->d_pairs = dp;
+    b->d_tiles2 = dt;
+    b->d_err = de;
     return cudaSuccess;
 }
 
