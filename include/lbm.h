@@ -318,8 +318,13 @@ int lbm_batch_sync(lbm_batch_t b);
  * the arrays trade roles at every launch.  lbm_batch_step then takes pairs of
  * steps from even steps and single batched steps for an odd start or end; a
  * call whose lattices are at steps of different parity takes single steps
- * only.  Results are bit for bit those of single steps.  Errors: LBM_EINVAL
- * (a lattice smaller than 4 x 4 nodes), LBM_ENOMEM, LBM_ECUDA. */
+ * only.  Each launch runs one kernel per class of lattice (storage kind,
+ * walls, force, rounding) on streams of the batch's own, forked from and
+ * joined back to the batch stream; a lattice that changes its force or
+ * rounding between calls changes class, and the next call rebuilds the
+ * batch's tile list (waiting for its queued work first).  Results are bit for
+ * bit those of single steps.  Errors: LBM_EINVAL (a lattice smaller than
+ * 4 x 4 nodes), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_set_two_step(lbm_batch_t b, int on);
 
 /* cfg = (tile width, tile height in nodes, policy (0 round robin, 1 chunks,

@@ -18,12 +18,12 @@ cudaError_t launch_batch_bgk(int, const BatchDomain*, const int*, int, int, int,
                              cudaStream_t);
 cudaError_t launch_batch_rawmrt(int, const BatchDomain*, const int*, int, int, int, int, int, int*, const unsigned*, int,
                                 int, cudaStream_t);
-cudaError_t launch_batch_fused_cascaded(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
-                                        int, int*, cudaStream_t);
-cudaError_t launch_batch_fused_bgk(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int, int,
-                                   int*, cudaStream_t);
-cudaError_t launch_batch_fused_rawmrt(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
-                                      int, int*, cudaStream_t);
+cudaError_t launch_batch_fused_cascaded(int, int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*,
+                                        int, int, int*, cudaStream_t);
+cudaError_t launch_batch_fused_bgk(int, int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
+                                   int, int*, cudaStream_t);
+cudaError_t launch_batch_fused_rawmrt(int, int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*,
+                                      int, int, int*, cudaStream_t);
 
 // rtab[d * rstride + k] = the hash of (seed, t + base + k) of domain d, for the
 // k-th launch of a sequence that starts `base` steps after the domains' counts t.
@@ -72,7 +72,10 @@ struct lbm_batch_s {
     // Two steps per launch (lbm_batch_set_two_step, or chosen by the tuner):
     // every lattice's two arrays and their tensor maps (pinned staging and
     // device copy), the list of 64 x 16 tiles, the kernels' error word and a
-    // graph of two-step launches.
+    // graph of two-step launches.  The tile list is ordered by lattice class
+    // (class_first[c] .. class_first[c + 1] - 1 are the tiles of class c) for
+    // the classes in cls2; the kernels of the second and later classes of a
+    // launch run on branch streams forked from the batch stream.
     bool two_step = false;
     lbm::BatchPair* h_pairs = nullptr;
     lbm::BatchPair* d_pairs = nullptr;
@@ -80,6 +83,14 @@ struct lbm_batch_s {
     int ntiles2 = 0;
     int* d_err = nullptr;
     cudaGraphExec_t graph2 = nullptr;
+    std::vector<int> cls2;
+    int class_first[lbm::kBatchClasses + 1] = {};
+    struct Branch {
+        cudaStream_t s;
+        cudaEvent_t joined;  // recorded on s after its kernel; the batch stream waits on it
+    };
+    std::vector<Branch> branch;
+    cudaEvent_t fork = nullptr;  // recorded on the batch stream before a launch's branches
 };
 
 namespace {
@@ -139,9 +150,19 @@ cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int rows, int order) {
 
 // Copies each domain's current arguments and parity into the device table
 // (and, once two-step launches are prepared, each lattice's arrays and maps).
+cudaError_t order_tiles2(lbm_batch_s* b, int* dt);
+std::vector<int> domain_classes(const lbm_batch_s* b);
+
 cudaError_t refresh_domains(lbm_batch_s* b) {
     cudaError_t e = cudaEventSynchronize(b->done);  // the previous upload has finished reading h_doms
     if (e != cudaSuccess) return e;
+    if (b->h_pairs && domain_classes(b) != b->cls2) {  // a lattice changed its force or rounding
+        e = cudaStreamSynchronize(b->stream);  // no launch still reads the tile list
+        if (e == cudaSuccess) e = order_tiles2(b, b->d_tiles2);
+        if (e != cudaSuccess) return e;
+        if (b->graph2) cudaGraphExecDestroy(b->graph2);
+        b->graph2 = nullptr;
+    }
     if (b->h_pairs) {
         for (size_t i = 0; i < b->doms.size(); ++i) {
             const lbm_s* h = b->doms[i];
@@ -232,36 +253,79 @@ bool same_parity(const lbm_batch_s* b) {
     return true;
 }
 
-// Second arrays and tensor maps of every lattice, the 64 x 16 tile list (largest
-// lattice first) and the error word; made once.
-cudaError_t prepare_two_step(lbm_batch_s* b) {
-    if (b->h_pairs) return cudaSuccess;
-    cudaError_t e = cudaSuccess;
-    for (lbm_s* h : b->doms)
-        if (e == cudaSuccess) e = lbm_prepare_two_step(h);
+std::vector<int> domain_classes(const lbm_batch_s* b) {
+    std::vector<int> c;
+    for (const lbm_s* h : b->doms) c.push_back(lbm::batch_class(h->store, h->walls, lbm::force_mode(h), h->a.rseed != 0));
+    return c;
+}
+
+// The 64 x 16 tiles of every lattice into dt, ordered by class and within a
+// class largest lattice first; records the class ranges and the classes, and
+// makes a branch stream for every class present after the first.
+cudaError_t order_tiles2(lbm_batch_s* b, int* dt) {
+    const std::vector<int> cls = domain_classes(b);
     std::vector<int> idx(b->doms.size());
     std::iota(idx.begin(), idx.end(), 0);
+    auto nodes = [&](int d) { return (long long)b->doms[d]->a.nx * b->doms[d]->a.ny; };
     std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) {
-        return (long long)b->doms[p]->a.nx * b->doms[p]->a.ny > (long long)b->doms[q]->a.nx * b->doms[q]->a.ny;
+        return cls[p] != cls[q] ? cls[p] < cls[q] : nodes(p) > nodes(q);
     });
     std::vector<int> t;
+    int first[lbm::kBatchClasses + 1] = {};
     for (int d : idx) {
         const int tx = (b->doms[d]->a.nx + lbm::kBatchFusedTX - 1) / lbm::kBatchFusedTX;
         const int ty = (b->doms[d]->a.ny + lbm::kBatchFusedTY - 1) / lbm::kBatchFusedTY;
         for (int j = 0; j < ty; ++j)
             for (int i = 0; i < tx; ++i) t.insert(t.end(), {d, i, j});
+        first[cls[d] + 1] += tx * ty;
     }
+    int present = 0;
+    for (int c = 0; c < lbm::kBatchClasses; ++c) {
+        present += first[c + 1] > 0;
+        first[c + 1] += first[c];
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && int(b->branch.size()) < present - 1) {
+        lbm_batch_s::Branch br{nullptr, nullptr};
+        e = cudaStreamCreateWithFlags(&br.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&br.joined, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            b->branch.push_back(br);
+        } else {
+            if (br.s) cudaStreamDestroy(br.s);
+            if (br.joined) cudaEventDestroy(br.joined);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // t is a local vector
+    if (e != cudaSuccess) return e;
+    std::copy(first, first + lbm::kBatchClasses + 1, b->class_first);
+    b->cls2 = cls;
+    return cudaSuccess;
+}
+
+// Second arrays and tensor maps of every lattice, the 64 x 16 tile list and
+// the error word; made once.
+cudaError_t prepare_two_step(lbm_batch_s* b) {
+    if (b->h_pairs) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (lbm_s* h : b->doms)
+        if (e == cudaSuccess) e = lbm_prepare_two_step(h);
+    size_t ntiles = 0;  // fewer than the one-step list's, whose size lbm_batch_create bounds
+    for (const lbm_s* h : b->doms)
+        ntiles += size_t((h->a.nx + lbm::kBatchFusedTX - 1) / lbm::kBatchFusedTX) *
+                  ((h->a.ny + lbm::kBatchFusedTY - 1) / lbm::kBatchFusedTY);
     lbm::BatchPair* hp = nullptr;
     lbm::BatchPair* dp = nullptr;
     int* dt = nullptr;
     int* de = nullptr;
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hp, b->doms.size() * sizeof(lbm::BatchPair));
     if (e == cudaSuccess) e = cudaMalloc((void**)&dp, b->doms.size() * sizeof(lbm::BatchPair));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&dt, t.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dt, 3 * ntiles * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&de, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(de, 0, sizeof(int), b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // t is a local vector
+    if (e == cudaSuccess) e = order_tiles2(b, dt);
     if (e != cudaSuccess) {  // nothing kept: a later call starts over
         if (hp) cudaFreeHost(hp);
         if (dp) cudaFree(dp);
@@ -269,7 +333,7 @@ cudaError_t prepare_two_step(lbm_batch_s* b) {
         if (de) cudaFree(de);
         return e;
     }
-    b->ntiles2 = int(t.size() / 3);
+    b->ntiles2 = int(ntiles);
     b->h_pairs = hp;
     b->d_pairs = dp;
     b->d_tiles2 = dt;
@@ -277,20 +341,46 @@ cudaError_t prepare_two_step(lbm_batch_s* b) {
     return cudaSuccess;
 }
 
-// Two-step launch k of a sequence (reads each lattice's arr[k & 1]); the round
-// table holds rstride hashes per lattice, two per launch from 2 kstep.
-cudaError_t launch_pair(lbm_batch_s* b, int k, int rstride, int kstep) {
+cudaError_t launch_class(lbm_batch_s* b, int c, int k, int rstride, int kstep, cudaStream_t s) {
+    const int n = b->class_first[c + 1] - b->class_first[c];
+    const int* tiles = b->d_tiles2 + 3 * b->class_first[c];
     switch (b->model) {
         case LBM_CASCADED:
-            return lbm::launch_batch_fused_cascaded(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride,
-                                                    kstep, b->d_err, b->stream);
+            return lbm::launch_batch_fused_cascaded(c, n, b->d_doms, b->d_pairs, tiles, k, b->d_rtab, rstride, kstep,
+                                                    b->d_err, s);
         case LBM_BGK:
-            return lbm::launch_batch_fused_bgk(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride, kstep,
-                                               b->d_err, b->stream);
+            return lbm::launch_batch_fused_bgk(c, n, b->d_doms, b->d_pairs, tiles, k, b->d_rtab, rstride, kstep,
+                                               b->d_err, s);
         default:
-            return lbm::launch_batch_fused_rawmrt(b->ntiles2, b->d_doms, b->d_pairs, b->d_tiles2, k, b->d_rtab, rstride,
-                                                  kstep, b->d_err, b->stream);
+            return lbm::launch_batch_fused_rawmrt(c, n, b->d_doms, b->d_pairs, tiles, k, b->d_rtab, rstride, kstep,
+                                                  b->d_err, s);
     }
+}
+
+// Two-step launch k of a sequence (reads each lattice's arr[k & 1]); the round
+// table holds rstride hashes per lattice, two per launch from 2 kstep.  One
+// kernel per class present: the first on the batch stream, each other one on a
+// branch stream that waits for the batch stream and that the batch stream then
+// waits for, so the kernels run side by side (also inside a captured graph).
+cudaError_t launch_pair(lbm_batch_s* b, int k, int rstride, int kstep) {
+    int used[lbm::kBatchClasses];
+    int n = 0;
+    for (int c = 0; c < lbm::kBatchClasses; ++c)
+        if (b->class_first[c + 1] > b->class_first[c]) used[n++] = c;
+    if (n > int(b->branch.size()) + 1) return cudaErrorInvalidValue;
+    cudaError_t e = n > 1 ? cudaEventRecord(b->fork, b->stream) : cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        if (i == 0) {
+            e = launch_class(b, used[0], k, rstride, kstep, b->stream);
+            continue;
+        }
+        const lbm_batch_s::Branch& br = b->branch[i - 1];
+        e = cudaStreamWaitEvent(br.s, b->fork, 0);
+        if (e == cudaSuccess) e = launch_class(b, used[i], k, rstride, kstep, br.s);
+        if (e == cudaSuccess) e = cudaEventRecord(br.joined, br.s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, br.joined, 0);
+    }
+    return e;
 }
 
 // Launches per replay of the two-step graph: graph_steps / 2, rounded down to an
@@ -480,6 +570,12 @@ int lbm_batch_destroy(lbm_batch_t b) {
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_doms) cudaFree(b->d_doms);
     if (b->h_doms) cudaFreeHost(b->h_doms);
+    for (const lbm_batch_s::Branch& br : b->branch) {
+        cudaStreamSynchronize(br.s);
+        cudaEventDestroy(br.joined);
+        cudaStreamDestroy(br.s);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->done) cudaEventDestroy(b->done);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -14,8 +14,9 @@ int batch_blocks_per_sm_bgk() {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<LBM_BGK>, kBatchThreads, 0) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
-cudaError_t launch_batch_fused_bgk(int ntiles, const BatchDomain* doms, const BatchPair* pairs, const int* tiles, int k,
-                                  const unsigned* rtab, int rstride, int kstep, int* err, cudaStream_t s) {
-    return launch_batch_fused_model<LBM_BGK>(ntiles, doms, pairs, tiles, k, rtab, rstride, kstep, err, s);
+cudaError_t launch_batch_fused_bgk(int cls, int ntiles, const BatchDomain* doms, const BatchPair* pairs,
+                                  const int* tiles, int k, const unsigned* rtab, int rstride, int kstep, int* err,
+                                  cudaStream_t s) {
+    return launch_batch_fused_model<LBM_BGK>(cls, ntiles, doms, pairs, tiles, k, rtab, rstride, kstep, err, s);
 }
 }  // namespace lbm

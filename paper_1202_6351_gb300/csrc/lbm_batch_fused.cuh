@@ -10,7 +10,18 @@
 // within a launch (each reads its halo from the input array and writes only its
 // own nodes to the output array), and the lattices are independent of each
 // other, so no CTA waits on another.
+//
+// The lattices fall into classes by storage kind, edges, force and rounding
+// (the template arguments of the tile body).  The tile list is ordered by
+// class and each class has a kernel of its own, so every kernel carries one
+// tile body under its register budget, as the single-lattice kernel does; the
+// kernels of one two-step launch are independent and run side by side.  Every
+// class collides one node per thread: the packed FP32x2 node pairs of the
+// single-lattice kernel spill here (the tile decode takes registers of its
+// own) and ran slower.
 #pragma once
+
+#include <utility>
 
 #include "lbm_batch_impl.cuh"
 #include "lbm_fused.cuh"
@@ -25,50 +36,26 @@ struct alignas(64) BatchPair {
     void* arr[2];
 };
 
-// Shared memory of the two-step batch kernel: the largest tile buffer of the
-// storage kinds a batch may hold.
-constexpr size_t kBatchFusedSmem =
-    FusedGeom<LBM_F32>::SMEM > FusedGeom<LBM_F16DEV>::SMEM ? FusedGeom<LBM_F32>::SMEM : FusedGeom<LBM_F16DEV>::SMEM;
 static_assert(FusedTile<LBM_F32>::THREADS == FusedTile<LBM_F16DEV>::THREADS &&
                   FusedGeom<LBM_F32>::TX == FusedGeom<LBM_F16DEV>::TX && FusedGeom<LBM_F32>::TY == FusedGeom<LBM_F16DEV>::TY,
               "one tile shape and CTA size for every storage kind");
 constexpr int kBatchFusedThreads = FusedTile<LBM_F32>::THREADS;
-// The packed FP32x2 stages of the two-step tile (lbm_fused.cuh) in the batch
-// kernel, which carries every storage, edge, force and rounding path in one
-// kernel.
-constexpr bool kBatchPacked = false;
 constexpr int kBatchFusedTX = FusedGeom<LBM_F32>::TX, kBatchFusedTY = FusedGeom<LBM_F32>::TY;
 
-template <int MODEL, int STORE, int FORCE, bool WALLS>
-__device__ __forceinline__ void batch_fused_sr(const BatchPair& P, const Args& a, int src, int* err, int x0, int y0,
-                                               unsigned rb0, unsigned rb1, unsigned char* smem,
-                                               unsigned long long* bar, int* ok) {
-    if (a.rseed)
-        fused2_tile<MODEL, STORE, FORCE, WALLS, true, kBatchPacked>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0,
-                                                                    y0, rb0, rb1, smem, bar, ok);
-    else
-        fused2_tile<MODEL, STORE, FORCE, WALLS, false, kBatchPacked>(&P.map[src], a, P.arr[src], P.arr[src ^ 1], err, x0,
-                                                                     y0, 0u, 0u, smem, bar, ok);
+// Class of a lattice: storage kind (FP32, FP16, BF16 deviations), any wall,
+// uniform force, stochastic rounding.
+constexpr int kBatchClasses = 24;
+inline int batch_class(int store, bool walls, int force, bool sr) {
+    const int s = store == LBM_F32 ? 0 : (store == LBM_F16DEV ? 1 : 2);
+    return ((s * 2 + (walls ? 1 : 0)) * 2 + (force ? 1 : 0)) * 2 + (sr ? 1 : 0);
 }
 
-template <int MODEL, int STORE>
-__device__ __forceinline__ void batch_fused_store(const BatchDomain& D, const BatchPair& P, int src, int* err, int x0,
-                                                  int y0, unsigned rb0, unsigned rb1, unsigned char* smem,
-                                                  unsigned long long* bar, int* ok) {
-    if (D.walls) {
-        if (D.force) batch_fused_sr<MODEL, STORE, 1, true>(P, D.a, src, err, x0, y0, rb0, rb1, smem, bar, ok);
-        else batch_fused_sr<MODEL, STORE, 0, true>(P, D.a, src, err, x0, y0, rb0, rb1, smem, bar, ok);
-    } else {
-        if (D.force) batch_fused_sr<MODEL, STORE, 1, false>(P, D.a, src, err, x0, y0, rb0, rb1, smem, bar, ok);
-        else batch_fused_sr<MODEL, STORE, 0, false>(P, D.a, src, err, x0, y0, rb0, rb1, smem, bar, ok);
-    }
-}
-
-// tiles: 3 ints per tile (lattice, tile x, tile y) of 64 x 16 nodes; launch k
-// of a sequence reads arr[k & 1]; the stochastic-rounding hashes of its two
-// steps are rtab[d * rstride + 2 kstep] and [... + 1].
-template <int MODEL>
-__global__ void __launch_bounds__(kBatchFusedThreads, FusedTile<LBM_F32>::MIN_BLOCKS)
+// tiles: 3 ints per tile (lattice, tile x, tile y) of 64 x 16 nodes, every
+// lattice of this kernel's class; launch k of a sequence reads arr[k & 1];
+// the stochastic-rounding hashes of its two steps are
+// rtab[d * rstride + 2 kstep] and [... + 1].
+template <int MODEL, int STORE, int FORCE, bool WALLS, bool SR>
+__global__ void __launch_bounds__(FusedTile<STORE>::THREADS, FusedTile<STORE>::MIN_BLOCKS)
     batch_fused_kernel(const BatchDomain* __restrict__ doms, const BatchPair* __restrict__ pairs,
                        const int* __restrict__ tiles, int k, const unsigned* __restrict__ rtab, int rstride, int kstep,
                        int* __restrict__ err) {
@@ -84,37 +71,54 @@ __global__ void __launch_bounds__(kBatchFusedThreads, FusedTile<LBM_F32>::MIN_BL
         for (int c = threadIdx.x; c < kDomChunks; c += blockDim.x) dst[c] = src[c];
     }
     __syncthreads();
-    const BatchDomain& D = sdom;
     const BatchPair& P = pairs[dom];
-    unsigned rb0 = 0u, rb1 = 0u;
-    if (D.a.rseed) {
-        rb0 = rtab[dom * rstride + 2 * kstep];
-        rb1 = rtab[dom * rstride + 2 * kstep + 1];
-    }
+    const unsigned rb0 = SR ? rtab[dom * rstride + 2 * kstep] : 0u;
+    const unsigned rb1 = SR ? rtab[dom * rstride + 2 * kstep + 1] : 0u;
     const int src = k & 1;
-    const int x0 = tx * kBatchFusedTX, y0 = ty * kBatchFusedTY;
-    switch (D.store) {
-        case LBM_F32: batch_fused_store<MODEL, LBM_F32>(D, P, src, err, x0, y0, rb0, rb1, fused_smem, &bar, &ok); break;
-        case LBM_F16DEV: batch_fused_store<MODEL, LBM_F16DEV>(D, P, src, err, x0, y0, rb0, rb1, fused_smem, &bar, &ok); break;
-        default: batch_fused_store<MODEL, LBM_BF16DEV>(D, P, src, err, x0, y0, rb0, rb1, fused_smem, &bar, &ok); break;
-    }
+    fused2_tile<MODEL, STORE, FORCE, WALLS, SR, false>(&P.map[src], sdom.a, P.arr[src], P.arr[src ^ 1], err,
+                                                       tx * kBatchFusedTX, ty * kBatchFusedTY, rb0, rb1, fused_smem,
+                                                       &bar, &ok);
 }
 
-template <int MODEL>
-static cudaError_t launch_batch_fused_model(int ntiles, const BatchDomain* doms, const BatchPair* pairs, const int* tiles,
-                                            int k, const unsigned* rtab, int rstride, int kstep, int* err,
-                                            cudaStream_t s) {
+template <int MODEL, int CLS>
+static cudaError_t launch_batch_class(int ntiles, const BatchDomain* doms, const BatchPair* pairs, const int* tiles,
+                                      int k, const unsigned* rtab, int rstride, int kstep, int* err, cudaStream_t s) {
+    constexpr int STORE = CLS / 8 == 0 ? LBM_F32 : (CLS / 8 == 1 ? LBM_F16DEV : LBM_BF16DEV);
+    constexpr bool WALLS = (CLS / 4) & 1, SR = CLS & 1;
+    constexpr int FORCE = (CLS / 2) & 1;
+    constexpr size_t SMEM = FusedGeom<STORE>::SMEM;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(batch_fused_kernel<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(kBatchFusedSmem));
+        cudaError_t e = cudaFuncSetAttribute(batch_fused_kernel<MODEL, STORE, FORCE, WALLS, SR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
         if (e != cudaSuccess) return e;
         configured = true;
     }
     if (ntiles < 1) return cudaSuccess;
-    batch_fused_kernel<MODEL><<<ntiles, kBatchFusedThreads, kBatchFusedSmem, s>>>(doms, pairs, tiles, k, rtab, rstride,
-                                                                                  kstep, err);
+    batch_fused_kernel<MODEL, STORE, FORCE, WALLS, SR><<<ntiles, kBatchFusedThreads, SMEM, s>>>(
+        doms, pairs, tiles, k, rtab, rstride, kstep, err);
     return cudaGetLastError();
+}
+
+using BatchClassLaunch = cudaError_t (*)(int, const BatchDomain*, const BatchPair*, const int*, int, const unsigned*, int,
+                                         int, int*, cudaStream_t);
+
+template <int MODEL, int... C>
+static cudaError_t launch_batch_fused_class(std::integer_sequence<int, C...>, int cls, int ntiles,
+                                            const BatchDomain* doms, const BatchPair* pairs, const int* tiles, int k,
+                                            const unsigned* rtab, int rstride, int kstep, int* err, cudaStream_t s) {
+    static constexpr BatchClassLaunch table[] = {launch_batch_class<MODEL, C>...};
+    if (cls < 0 || cls >= int(sizeof...(C))) return cudaErrorInvalidValue;
+    return table[cls](ntiles, doms, pairs, tiles, k, rtab, rstride, kstep, err, s);
+}
+
+// The kernel of class `cls` over `ntiles` tiles of that class.
+template <int MODEL>
+static cudaError_t launch_batch_fused_model(int cls, int ntiles, const BatchDomain* doms, const BatchPair* pairs,
+                                            const int* tiles, int k, const unsigned* rtab, int rstride, int kstep,
+                                            int* err, cudaStream_t s) {
+    return launch_batch_fused_class<MODEL>(std::make_integer_sequence<int, kBatchClasses>(), cls, ntiles, doms, pairs,
+                                           tiles, k, rtab, rstride, kstep, err, s);
 }
 
 }  // namespace lbm

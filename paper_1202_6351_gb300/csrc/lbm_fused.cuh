@@ -222,19 +222,45 @@ __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& 
         return v < 0 ? v + n : (v >= n ? v - n : v);
     };
 
-    // periodic wrap-around of the region's halo (edge tiles only)
+    // periodic wrap-around of the region's halo (edge tiles only).  The nodes of
+    // the tile depend on the region's cells within two nodes of the lattice,
+    // x in [-2, nx + 1] and y in [-2, ny + 1]; the cells of that ring outside the
+    // lattice across a periodic edge are fetched from their images.  Region
+    // cells further out (a tile cut by the lattice's edge) keep the zeros of the
+    // tensor load: they are collided but feed no node of the lattice, since in
+    // both steps every slot is read and written by one node only.
     if ((perx && (x0 - 2 < 0 || x0 + G::TX + 2 > a.nx)) || (pery && (y0 - 2 < 0 || y0 + G::TY + 2 > a.ny))) {
         const T* __restrict__ f = static_cast<const T*>(in);
-        for (int k = tid; k < 9 * G::RW * G::RH; k += NT) {
-            const int q = k / (G::RW * G::RH), r = k % (G::RW * G::RH);
-            const int ry = r / G::RW, rx = r % G::RW;
-            int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-            const bool outx = gx < 0 || gx >= a.nx, outy = gy < 0 || gy >= a.ny;
-            if (!((outx && perx) || (outy && pery))) continue;
-            if ((outx && !perx) || (outy && !pery)) continue;  // beyond a wall: never used
-            gx = ((gx % a.nx) + a.nx) % a.nx;
-            gy = ((gy % a.ny) + a.ny) % a.ny;
-            Aat(q, ry, rx + G::OFF) = f[q * a.plane + (long long)gy * a.pitch + gx];
+        const int X0 = x0 - 2, Y0 = y0 - 2;                 // region origin (>= -2)
+        const int X1 = min(x0 + G::TX + 2, a.nx + 2);        // ring end along x
+        const int Y1 = min(y0 + G::TY + 2, a.ny + 2);
+        const int xi0 = max(X0, 0), xi1 = min(X1, a.nx);     // columns inside the lattice
+        const int yi0 = max(Y0, 0), yi1 = min(Y1, a.ny);
+        // rows outside the lattice (periodic y): below 0, then from ny; each over
+        // the ring's columns (all of them if x is periodic, else those inside)
+        const int rlo = pery ? max(0, min(0, Y1) - Y0) : 0;
+        const int rhi = pery ? max(0, Y1 - max(a.ny, Y0)) : 0;
+        const int rx0 = perx ? X0 : xi0, rw = max(0, (perx ? X1 : xi1) - rx0);
+        // columns outside the lattice (periodic x), over the rows inside it
+        const int clo = perx ? max(0, min(0, X1) - X0) : 0;
+        const int chi = perx ? max(0, X1 - max(a.nx, X0)) : 0;
+        const int ch = max(0, yi1 - yi0);
+        const int nrow = (rlo + rhi) * rw, ncell = nrow + (clo + chi) * ch;
+        for (int k = tid; k < ncell; k += NT) {
+            int gx, gy;
+            if (k < nrow) {
+                const int r = k / rw;
+                gx = rx0 + (k - r * rw);
+                gy = r < rlo ? Y0 + r : max(a.ny, Y0) + (r - rlo);
+            } else {
+                const int c = (k - nrow) / ch;
+                gy = yi0 + (k - nrow - c * ch);
+                gx = c < clo ? X0 + c : max(a.nx, X0) + (c - clo);
+            }
+            const int ry = gy - Y0, rx = gx - X0;
+            const long long src = (long long)(((gy % a.ny) + a.ny) % a.ny) * a.pitch + ((gx % a.nx) + a.nx) % a.nx;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Aat(q, ry, rx + G::OFF) = f[q * a.plane + src];
         }
         __syncthreads();
     }

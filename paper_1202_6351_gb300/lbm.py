@@ -264,7 +264,7 @@ class Lattice:
         return self
 
     def set_rounding(self, mode, seed=0):
-        """ROUND_NEAREST or ROUND_STOCHASTIC (16-bit storage) with a seed."""
+        """ROUND_NEAREST or ROUND_STOCHASTIC (16-bit or FP32 storage) with a seed."""
         _check(self.lib.lbm_set_rounding(self.h, int(mode), int(seed) & (2 ** 64 - 1)))
         return self
 

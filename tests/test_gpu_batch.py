@@ -129,6 +129,48 @@ def test_batch_two_steps_per_launch_is_bitwise_equal_to_single_steps(start, roun
         L.close()
 
 
+def test_batch_two_step_follows_lattices_that_change_force_or_rounding():
+    """The two-step batch runs one kernel per class of lattice (storage kind,
+    walls, force, rounding).  A lattice that turns its force or stochastic
+    rounding on or off between batch calls moves to another class; the
+    following launches (graph replays included) must take it along and still
+    match single steps bit for bit."""
+    alone = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+    batched = [make(s, i) for i, s in enumerate(DOMAINS_TWO_STEP)]
+
+    def change(Ls, phase):
+        if phase == 0:
+            Ls[0].set_rounding(lbm.ROUND_STOCHASTIC, 11)  # FP32 periodic: leaves the packed class
+            Ls[3].set_force((3e-5, -1e-5))  # FP16 periodic, now forced
+            Ls[2].set_force((0.0, 0.0))  # BF16 with walls, now unforced
+        else:
+            Ls[0].set_rounding(lbm.ROUND_NEAREST)
+            Ls[7].set_rounding(lbm.ROUND_STOCHASTIC, 5)
+
+    with lbm.Batch(batched) as B:
+        B.set_graph_steps(8)
+        B.set_two_step(True)
+        B.step(10)
+        change(batched, 0)
+        B.step(12)
+        change(batched, 1)
+        B.step(8)
+        B.sync()
+    for L in alone:
+        L.step(10)
+    change(alone, 0)
+    for L in alone:
+        L.step(12)
+    change(alone, 1)
+    for L in alone:
+        L.step(8)
+    for i, (a, b) in enumerate(zip(alone, batched)):
+        assert a.time == b.time
+        np.testing.assert_array_equal(a.get_f(), b.get_f(), err_msg=f"domain {i}")
+    for L in alone + batched:
+        L.close()
+
+
 def test_batch_tuner_with_the_two_step_candidate_leaves_states_unchanged():
     """The batch tuner also times two steps per launch when every lattice admits
     it and all are at the same even step; its trial launches swap each
