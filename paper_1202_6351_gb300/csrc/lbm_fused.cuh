@@ -28,6 +28,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "lbm_async.cuh"
 #include "lbm_device.cuh"
 #include "lbm_pair.cuh"
@@ -310,45 +312,59 @@ __device__ __forceinline__ void fused2_tile(const CUtensorMap* map, const Args& 
     // wall from the node's own slot q; it leaves into slot q of the node at
     // x + e_q, or through a wall into the node's own slot opp(q); each slot is
     // read and written by one node only)
-    for (int k = tid; k < G::SW * G::SH; k += NT) {
-        const int sy = k / G::SW, sx = k % G::SW;
-        int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
-        if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
-        gx = wrap(gx, a.nx);
-        gy = wrap(gy, a.ny);
-        const int ry = sy + 1, rxb = sx + 1 + G::OFF;
-        R d[9], e[9];
+    // A tile whose grown region holds no node next to a wall runs the body
+    // without wall links: incoming_wall finds none there, so the arithmetic is
+    // the same.
+    auto odd_step = [&](auto walls_tag) {
+        constexpr bool WL = decltype(walls_tag)::value;
+        for (int k = tid; k < G::SW * G::SH; k += NT) {
+            const int sy = k / G::SW, sx = k % G::SW;
+            int gx = x0 - 1 + sx, gy = y0 - 1 + sy;
+            if ((!perx && (gx < 0 || gx >= a.nx)) || (!pery && (gy < 0 || gy >= a.ny))) continue;
+            gx = wrap(gx, a.nx);
+            gy = wrap(gy, a.ny);
+            const int ry = sy + 1, rxb = sx + 1 + G::OFF;
+            R d[9], e[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int w = WALLS ? incoming_wall(a, q, gx, gy) : -1;
-            if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(q, ry, rxb)), q, w);
-            else d[q] = S::dec(Aat(opp(q), ry - cy(q), rxb - cx(q)));
-        }
-        R Fx, Fy;
-        node_force<R, FORCE>(a, gx, gy, Fx, Fy);
-        collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
-        const unsigned rn = SR ? round_node(a, rb1, gx, gy) : 0u;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
-            const int w = WALLS ? incoming_wall(a, opp(q), gx, gy) : -1;
-            R v = d[q], ev = TS ? e[q] : R(0);
-            if (w >= 0) {
-                if constexpr (TS) {
-                    float e2;
-                    v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
-                    ev = e[q] + e2;
-                } else {
-                    v = add_wall_term<R>(a, d[q], opp(q), w);
-                }
+            for (int q = 0; q < 9; ++q) {
+                const int w = WL ? incoming_wall(a, q, gx, gy) : -1;
+                if (w >= 0) d[q] = add_wall_term<R>(a, S::dec(Aat(q, ry, rxb)), q, w);
+                else d[q] = S::dec(Aat(opp(q), ry - cy(q), rxb - cx(q)));
             }
-            T o;
-            if constexpr (TS) o = round_sr32(v, ev, r);
-            else if constexpr (SR) o = enc_sr<STORE>(v, r);
-            else o = S::enc(v);
-            if (w >= 0) Aat(opp(q), ry, rxb) = o;
-            else Aat(q, ry + cy(q), rxb + cx(q)) = o;
+            R Fx, Fy;
+            node_force<R, FORCE>(a, gx, gy, Fx, Fy);
+            collide<MODEL, R, (FORCE != 0), TS>(d, Fx, Fy, c, e);
+            const unsigned rn = SR ? round_node(a, rb1, gx, gy) : 0u;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const unsigned r = rn + static_cast<unsigned>(q) * kRoundStride;
+                const int w = WL ? incoming_wall(a, opp(q), gx, gy) : -1;
+                R v = d[q], ev = TS ? e[q] : R(0);
+                if (w >= 0) {
+                    if constexpr (TS) {
+                        float e2;
+                        v = two_sum(d[q], wall_term<R>(a, opp(q), w), e2);
+                        ev = e[q] + e2;
+                    } else {
+                        v = add_wall_term<R>(a, d[q], opp(q), w);
+                    }
+                }
+                T o;
+                if constexpr (TS) o = round_sr32(v, ev, r);
+                else if constexpr (SR) o = enc_sr<STORE>(v, r);
+                else o = S::enc(v);
+                if (w >= 0) Aat(opp(q), ry, rxb) = o;
+                else Aat(q, ry + cy(q), rxb + cx(q)) = o;
+            }
         }
+    };
+    if constexpr (WALLS) {
+        const bool near_wall = (a.wall[LBM_WEST] && x0 - 1 <= 0) || (a.wall[LBM_EAST] && x0 + G::TX >= a.nx - 1) ||
+                               (a.wall[LBM_SOUTH] && y0 - 1 <= 0) || (a.wall[LBM_NORTH] && y0 + G::TY >= a.ny - 1);
+        if (near_wall) odd_step(std::true_type{});
+        else odd_step(std::false_type{});
+    } else {
+        odd_step(std::false_type{});
     }
     }  // one node per thread
     fence_async_shared();  // the odd step's shared-memory writes before the bulk stores read them

@@ -594,6 +594,9 @@ FUSED_CASES = [  # (nx, ny, edges, force, force field, store, rounding)
     (4, 4, "cavity", (0.0, 0.0), False, lbm.F16DEV, False),
     (90, 40, "allmoving", (1e-5, -2e-5), False, lbm.F32, False),
     (77, 50, "ychannel", (0.0, 3e-5), False, lbm.BF16DEV, True),
+    # tiles away from every wall (the odd step's body without wall links) beside tiles at the walls
+    (260, 70, "cavity", (0.0, 0.0), False, lbm.F32, True),
+    (200, 70, "channel", (2e-5, 1e-5), False, lbm.F16DEV, False),
     # periodic, unforced FP32: the cascaded collision runs in packed FP32x2 pairs here
     (130, 33, "periodic", (0.0, 0.0), False, lbm.F32, False),
     (64, 16, "periodic", (0.0, 0.0), False, lbm.F32, False),
