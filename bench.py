@@ -662,9 +662,10 @@ def run_d3q27_extras(lbm, torch, peak, sp, n=256, steps=100):
 def run_batch_extras(lbm, torch, np, peak, sp, steps=200, count=96):
     """Batched ensemble: 96 domains (sides log-uniform in [64, 2048], half
     lid-driven cavities at Re in [100, 5000], half Taylor-Green, FP32 / FP16
-    storage), one persistent launch per step under CUDA graphs of 100 steps,
-    against one lbm_step launch per domain per step; plus the 16384^2 FP16
-    cavity at Re = 5000 as the single-domain roofline point."""
+    storage), advanced together in the configuration the batch tuner keeps (one
+    launch per step over all tiles, or one launch per two steps with a kernel
+    per class of lattice) under CUDA graphs of 100 steps, against one lbm_step
+    launch per domain per step."""
     from paper_1202_6351_gb300 import workloads
 
     doms = workloads.batch_domains()[:count]  # fewer domains only for profiling captures
@@ -699,7 +700,7 @@ def run_batch_extras(lbm, torch, np, peak, sp, steps=200, count=96):
     e1.record(stream)
     torch.cuda.synchronize()
     t_sep = e0.elapsed_time(e1) / 1e3
-    # one persistent launch per step, graphs of 100 steps, autotuned
+    # all lattices in one batch, graphs of 100 steps, autotuned
     B = lbm.Batch(Ls)
     tuned_ms = B.tune(5)
     info = B.info()

@@ -269,8 +269,9 @@ int lbm_adjoint_run(lbm_t h, long nsteps, long every, const double* rho, const d
 /* ---------------------------------------------------------------------------
  * Batches: many independent lattices advanced together (no counterpart in the
  * paper).  One time step of every lattice in the batch is ONE launch of a
- * persistent kernel whose CTAs walk a work list of (lattice, tile) items; the
- * per-node update is exactly that of lbm_step, so results are bitwise equal.
+ * kernel whose CTAs walk a work list of (lattice, tile) items, or two steps
+ * are one launch per class of lattice (lbm_batch_set_two_step); the per-node
+ * update is exactly that of lbm_step, so results are bitwise equal.
  * Chunks of `graph_steps` steps (default 100, even) are replayed from a CUDA
  * graph.  All lattices must share the device and the collision model, use
  * LBM_F32, LBM_BF16DEV or LBM_F16DEV storage and have no per-node force field;

@@ -1,7 +1,9 @@
-// lbm_batch.cu -- many independent lattices advanced together: one persistent
-// kernel launch per time step for all of them, CUDA graphs of `graph_steps`
-// launches, and an autotuner that picks the tile shape, the order of the work
-// list and the scheduling policy by timing them on the batch itself.
+// lbm_batch.cu -- many independent lattices advanced together: one kernel
+// launch per time step for all of them (a persistent grid walking a tile list,
+// or one CTA per tile), or one launch per two steps for each class of lattice
+// (lbm_batch_fused.cuh), CUDA graphs of `graph_steps` steps, and an autotuner
+// that picks the tile shape, the order of the work list and the scheduling
+// policy by timing them on the batch itself.
 #include <algorithm>
 #include <numeric>
 #include <vector>

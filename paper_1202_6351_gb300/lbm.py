@@ -376,7 +376,9 @@ class Lattice:
 
 
 class Batch:
-    """Many lattices advanced by one persistent launch per step (lbm_batch_*)."""
+    """Many lattices advanced together (lbm_batch_*): one launch per step over
+    all their tiles, or one launch per two steps (set_two_step; the tuner may
+    choose either)."""
 
     POLICIES = {0: "round_robin", 1: "chunked", 2: "dynamic", 3: "one_cta_per_tile", 4: "two_steps_per_launch"}
     ORDERS = {0: "largest_first", 1: "interleaved"}
