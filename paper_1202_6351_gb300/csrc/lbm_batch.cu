@@ -150,6 +150,18 @@ cudaError_t upload_tiles(lbm_batch_s* b, int lbx, int rows, int order) {
     return cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
 }
 
+// Waits for the batch stream and every branch stream.  After a complete
+// two-step launch the batch stream already waits for its branches; a launch
+// that failed half way may have left a branch kernel without that wait.
+cudaError_t sync_all(lbm_batch_s* b) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    for (const lbm_batch_s::Branch& br : b->branch) {
+        const cudaError_t e2 = cudaStreamSynchronize(br.s);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
+
 // Copies each domain's current arguments and parity into the device table
 // (and, once two-step launches are prepared, each lattice's arrays and maps).
 cudaError_t order_tiles2(lbm_batch_s* b, int* dt);
@@ -159,7 +171,7 @@ cudaError_t refresh_domains(lbm_batch_s* b) {
     cudaError_t e = cudaEventSynchronize(b->done);  // the previous upload has finished reading h_doms
     if (e != cudaSuccess) return e;
     if (b->h_pairs && domain_classes(b) != b->cls2) {  // a lattice changed its force or rounding
-        e = cudaStreamSynchronize(b->stream);  // no launch still reads the tile list
+        e = sync_all(b);  // no launch still reads the tile list
         if (e == cudaSuccess) e = order_tiles2(b, b->d_tiles2);
         if (e != cudaSuccess) return e;
         if (b->graph2) cudaGraphExecDestroy(b->graph2);
@@ -561,7 +573,7 @@ int lbm_batch_create(const lbm_t* lattices, int count, lbm_batch_t* out) {
 int lbm_batch_destroy(lbm_batch_t b) {
     if (!b) return LBM_OK;
     Guard g(b->device);
-    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->stream) sync_all(b);
     drop_graph(b);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->h_pairs) cudaFreeHost(b->h_pairs);
@@ -573,7 +585,6 @@ int lbm_batch_destroy(lbm_batch_t b) {
     if (b->d_doms) cudaFree(b->d_doms);
     if (b->h_doms) cudaFreeHost(b->h_doms);
     for (const lbm_batch_s::Branch& br : b->branch) {
-        cudaStreamSynchronize(br.s);
         cudaEventDestroy(br.joined);
         cudaStreamDestroy(br.s);
     }
@@ -640,7 +651,7 @@ int lbm_batch_step(lbm_batch_t b, long n) {
 int lbm_batch_sync(lbm_batch_t b) {
     if (!b) return fail(LBM_EINVAL, "null batch");
     Guard g(b->device);
-    BATCH_CUDA(cudaStreamSynchronize(b->stream), "lbm_batch_sync");
+    BATCH_CUDA(sync_all(b), "lbm_batch_sync");
     if (b->d_err) {  // a two-step launch whose tile load timed out (cleared once reported)
         int v = 0;
         BATCH_CUDA(cudaMemcpy(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "lbm_batch_sync: error word");
