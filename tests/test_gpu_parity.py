@@ -310,6 +310,37 @@ def test_full_size_taylor_green_4096_sampled_nodes(store):
     torch.cuda.synchronize()
 
 
+def test_full_size_taylor_green_4096_two_steps_per_launch():
+    """The bench's tuned FP32 configuration (variant 3: two steps per launch,
+    node pairs in packed FP32x2, a graph replay of 64 steps among the 100) on
+    the bench workload: bit for bit the states of one step per launch after 2
+    and 102 steps, and sampled nodes (tile corners among them) after the first
+    two-step launch against the oracle."""
+    import torch
+
+    n, om = 4096, 1.6
+    rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+    out = {}
+    for variant in (0, 3):
+        g = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), store=lbm.F32)
+        g.set_variant(variant).init(rho, u)
+        assert g.info()["variant"] == variant
+        g.step(2)
+        f2 = g.get_f()
+        g.step(100)
+        out[variant] = (f2, g.get_f())
+        g.close()
+    np.testing.assert_array_equal(out[3][0], out[0][0])
+    np.testing.assert_array_equal(out[3][1], out[0][1])
+    f = out[3][0]
+    rng = np.random.default_rng(4097)
+    pts = [(0, 0), (n - 1, n - 1), (63, 15), (64, 16)] + [tuple(v) for v in rng.integers(0, n, (40, 2))]
+    for ix, iy in pts:
+        ref = _patch_reference((rho, u), om, ix, iy, 2)
+        assert np.abs(f[:, iy, ix] - ref).max() <= FULL_SIZE_TOL[lbm.F32], (ix, iy)
+    torch.cuda.synchronize()
+
+
 # ---------------------------------------------------------------- packed two-rows-per-thread variant
 
 @pytest.mark.parametrize("model", MODELS, ids=["cascaded", "bgk", "rawmrt"])
