@@ -245,3 +245,41 @@ def test_batch_rejects_unsupported_lattices():
         assert ei.value.code == lbm.LBM_EINVAL
     for L in (a, b, c):
         L.close()
+
+
+def test_full_size_96_domain_ensemble_two_steps_per_launch():
+    """The batched ensemble at full size (the 96 domains of
+    workloads.batch_domains(): sides 64..2048, lid-driven cavities at Re
+    100..5000 and Taylor-Green vortices, FP32 and FP16 storage, 52.9 M nodes)
+    in the configuration the bench's batch tuner keeps, two steps per launch
+    (one kernel per class of lattice, a graph replay among the launches):
+    every lattice ends bit for bit where it ends stepped alone."""
+    def build():
+        Ls = []
+        for d in workloads.batch_domains():
+            n = d["side"]
+            st = lbm.F32 if d["store"] == "f32" else lbm.F16DEV
+            if d["kind"] == "cavity":
+                U = 0.1
+                om = 1.0 / (3.0 * U * (n - 1) / d["re"] + 0.5)
+                L = lbm.Lattice(n, n, (1.0, om, om, 1.0, 1.0, 1.0), edges=(BB, BB, BB, MW), wall_u=(0, 0, 0, U),
+                                store=st).init()
+            else:
+                rho, u = workloads.taylor_green_init(n, workloads.diffusive_u0(n))
+                L = lbm.Lattice(n, n, (1.0, 1.6, 1.6, 1.0, 1.0, 1.0), store=st).init(rho, u)
+            Ls.append(L)
+        return Ls
+
+    batched = build()
+    with lbm.Batch(batched) as B:
+        B.set_graph_steps(8)
+        B.set_two_step(True)
+        B.step(10)  # one replay of four two-step launches, then one more launch
+        B.sync()
+    alone = build()
+    for i, (a, b) in enumerate(zip(alone, batched)):
+        a.step(10)
+        assert a.time == b.time == 10
+        np.testing.assert_array_equal(a.get_f(), b.get_f(), err_msg=f"domain {i} ({a.shape})")
+        a.close()
+        b.close()
